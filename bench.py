@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Benchmark: batched R-tree range select on GB300 (plus join and oracle baselines).
+
+One step = one pass of the whole hot path over one batch: STR bulk load of
+10M rectangles (80% in 64 Gaussian clusters, 20% uniform; sides log-uniform
+in [1e-5, 1e-3]) followed by a sorted range select of 1M square queries
+whose selectivity is log-uniform in [1e-6, 1e-3].  ``value`` = queries/s
+over the whole job (all ranks), inputs resident in HBM.  The node fanout and
+layout are picked once before the warm-up by timing one step of each
+candidate.  Under torchrun every rank builds and queries its own instance
+(weak scaling; no collective on the data path).
+
+``--impl reference`` times the CPU oracle (plain scalar C, one thread) on the
+same workload instead: the tree is built once, each step selects a fixed
+sample of queries, and ``value`` extrapolates to the full batch
+(1M / (build + per-query time * 1M)).
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "range queries/s at 10M rects"
+UNIT = "queries/s"
+WORKLOAD = "scaled"
+CPU_SAMPLE_QUERIES = 2000
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fanout", type=int, default=0, help="0: pick by timing 16/32/64")
+    ap.add_argument("--layout", choices=["soa", "aos", "auto"], default="auto")
+    ap.add_argument("--n", type=int, default=None, help="override rectangles (testing only)")
+    ap.add_argument("--q", type=int, default=None, help="override queries (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-join", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ ranks
+def dist_init(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under_load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": float(np.median(under_load)), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2309_16913_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"],
+                  "select_scatter": ["select.cu", "internal.cuh"],
+                  "sort_mid": ["segsort.cu"], "sort_small": ["segsort.cu"], "sort_large": ["segsort.cu"],
+                  "scatter": ["radix_sort.cu"], "join_count": ["join.cu", "internal.cuh"]}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    want = source_sha(KERNEL_SOURCES.get(kernel, []))
+    for line in open(path):
+        kv = dict(re.findall(r"(\w+)=(\S+)", line))
+        if kv.get("kernel") == kernel and kv.get("workload") == WORKLOAD:
+            if kv.get("source_sha") == want:
+                return float(kv["bytes_per_launch"]), kv.get("note")
+            return None, "kernel changed since the ncu capture"
+    return None, None
+
+
+def algorithmic_bytes(stats, F, Q, seg_sizes):
+    """Bytes each kernel must move, per launch (roofline)."""
+    node = F * 16 + 16                     # entry MBRs (all F slots) + node metadata
+    nodes = stats["nodes_visited"]
+    whole = stats["whole_children"] * 16   # metadata of children taken whole
+    hits = stats["ids"]
+    count = nodes * node + whole + Q * (16 + 4)
+    scatter = nodes * node + whole + Q * (16 + 16) + hits * (4 + 4)
+    mid = seg_sizes[(seg_sizes > 32) & (seg_sizes <= 4096)].sum() * 8
+    small = seg_sizes[(seg_sizes > 1) & (seg_sizes <= 32)].sum() * 8
+    large = seg_sizes[seg_sizes > 4096].sum() * 8 * 5
+    return {"select_count": float(count), "select_scatter": float(scatter),
+            "sort_mid": float(mid), "sort_small": float(small), "sort_large": float(large)}
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+
+    from paper_2309_16913_gb300 import build as build_mod
+    from paper_2309_16913_gb300 import datagen as dg
+
+    rank, local, world = dist_init("nccl")
+    torch.cuda.set_device(local)
+    build_mod.build()
+    from paper_2309_16913_gb300 import rtree as rt
+    rt.load_library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    seed = 1 + 1000 * rank
+    w = dg.workload(WORKLOAD, seed=seed, n=args.n, q=args.q)
+    N, Q = w.rects.shape[0], w.queries.shape[0]
+    rects = torch.from_numpy(w.rects).to(dev)
+    ids = torch.from_numpy(w.ids).to(dev)
+    queries = torch.from_numpy(w.queries).to(dev)
+    torch.cuda.synchronize()
+
+    def step(F, layout):
+        t = rt.RTree(rects, ids, fanout=F, layout=layout, stream=stream)
+        res = t.range_select(queries, stream=stream)
+        total = res.total
+        res.close()
+        t.close()
+        return total
+
+    # ---- pick fanout/layout by timing one step each (untimed for the result)
+    fanouts = [args.fanout] if args.fanout else [16, 32, 64]
+    layouts = ["soa", "aos"] if args.layout == "auto" else [args.layout]
+    sweep = {}
+    total_hits = None
+    for F in fanouts:
+        for lay in layouts:
+            step(F, lay)  # first touch / pool growth
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            total_hits = step(F, lay)
+            torch.cuda.synchronize()
+            sweep[f"F{F}_{lay}"] = round((time.perf_counter() - t0) * 1e3, 3)
+    best = min(sweep, key=sweep.get)
+    F = int(best.split("_")[0][1:])
+    layout = best.split("_")[1]
+
+    for _ in range(args.warmup):
+        step(F, layout)
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    rt.rtree_timing_reset()
+    rt.rtree_timing_enable(True)
+    launches0 = rt.rtree_launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(F, layout)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    rt.rtree_timing_enable(False)
+    ms_total = ev0.elapsed_time(ev1)
+    launches = rt.rtree_launch_count() - launches0
+    kern = rt.rtree_timing_get()
+    ms_max = max_over_ranks(ms_total, world, dev)
+    value = Q * args.steps * world / (ms_max / 1e3)
+
+    # ---- roofline of the dominant kernel
+    with rt.RTree(rects, ids, fanout=F, layout=layout) as t:
+        stats = t.select_stats(queries)
+        res = t.range_select(queries)
+        seg = np.diff(res.offsets_tensor().cpu().numpy())
+        res.close()
+    algo = algorithmic_bytes(stats, F, Q, seg)
+    hbm, peak_kind = peaks()
+    breakdown = {}
+    for name, (n_l, ms) in kern.items():
+        if n_l == 0:
+            continue
+        per = ms / n_l
+        entry = {"launches": n_l, "ms_total": round(ms, 3), "share": round(ms / max(1e-9, sum(v[1] for v in kern.values())), 4)}
+        if name in algo and per > 0:
+            entry["gbs"] = round(algo[name] / (per / 1e3) / 1e9, 1)
+        breakdown[name] = entry
+    dominant = max((k for k in kern if k in algo), key=lambda k: kern[k][1])
+    n_l, ms = kern[dominant]
+    achieved = algo[dominant] / ((ms / n_l) / 1e3) / 1e9
+    traffic, traffic_note = ncu_traffic(dominant)
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": algo[dominant],
+                "traffic": traffic}
+    if traffic_note:
+        roofline["traffic_note"] = traffic_note
+
+    # ---- end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        lib = rt.load_library()
+        h_rects = torch.from_numpy(w.rects).pin_memory()
+        h_ids = torch.from_numpy(w.ids).pin_memory()
+        h_q = torch.from_numpy(w.queries).pin_memory()
+        h_off = torch.empty(Q + 1, dtype=torch.int64).pin_memory()
+        h_out = torch.empty(max(1, int(total_hits)), dtype=torch.int32).pin_memory()
+        sptr = stream.cuda_stream
+
+        def e2e_step():
+            h = rt.rtree_build(h_rects, h_ids, F, layout, stream)
+            r = rt.rtree_range_select(h, h_q, stream=stream)
+            rc = lib.rtree_result_copy_to_host(r, h_off.data_ptr(), h_out.data_ptr(), sptr)
+            assert rc == 0, rt.rtree_last_error()
+            rt.rtree_result_free(r)
+            rt.rtree_free(h)
+
+        e2e_step()
+        k2 = max(1, min(args.steps, 3))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": round(Q * k2 * world / el, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.rects.nbytes + w.ids.nbytes + w.queries.nbytes),
+               "d2h_bytes_per_step": int(8 * (Q + 1) + 4 * int(total_hits)), "steps": k2}
+
+    # ---- join workload (R, S 2M each, fanout 32)
+    join = None
+    if not args.no_join:
+        j = dg.workload("join", seed=2 + 1000 * rank)
+        jr = torch.from_numpy(j.rects).to(dev)
+        js = torch.from_numpy(j.rects_s).to(dev)
+
+        def jstep():
+            a = rt.RTree(jr, None, fanout=32, stream=stream)
+            b = rt.RTree(js, None, fanout=32, stream=stream)
+            r = a.join(b, stream=stream)
+            tot = r.total
+            r.close(); a.close(); b.close()
+            return tot
+
+        pairs = jstep()
+        jstep()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kj = max(1, args.steps)
+        e0.record(stream)
+        for _ in range(kj):
+            jstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        jms = max_over_ranks(e0.elapsed_time(e1) / kj, world, dev)
+        join = {"metric": "join pairs/s (2M x 2M, build of both trees included)",
+                "value": round(pairs * world / (jms / 1e3), 1), "unit": "pairs/s",
+                "pairs": int(pairs), "ms_per_step": round(jms, 3)}
+
+    # ---- CPU oracle baseline (rank 0, one GPU runs only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_rate(w, F)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"scaled range select: {N} rects (80% 64-cluster gaussian, "
+                                   f"20% uniform, sides log-U[1e-5,1e-3]), {Q} queries "
+                                   "(selectivity log-U[1e-6,1e-3]), STR build + sorted select per step",
+                       "fanout": F, "layout": layout, "ids_returned_per_step": int(total_hits),
+                       "l2": "inputs larger than L2 (rects 160 MB, tree ~200 MB; no flush)",
+                       "sweep_ms_per_step": sweep, "seed": seed},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roofline,
+            "kernels": breakdown,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "join": join,
+            "select_stats": stats,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference
+def oracle_rate(w, F, sample=CPU_SAMPLE_QUERIES, build_s=None, steps=1):
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.Tree(w.rects, w.ids, F)
+    tb = time.perf_counter() - t0 if build_s is None else build_s
+    qs = w.queries[:sample]
+    t1 = time.perf_counter()
+    for _ in range(steps):
+        tree.select(qs)
+    per_q = (time.perf_counter() - t1) / (steps * qs.shape[0])
+    Q = w.queries.shape[0]
+    return {"value": round(Q / (tb + per_q * Q), 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle STR build of all {w.rects.shape[0]} rects ({tb:.2f} s) + sorted select "
+                      f"of the first {qs.shape[0]} queries ({per_q * 1e6:.1f} us/query), extrapolated "
+                      f"to {Q} queries: {Q} / (build + per_query * {Q})"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2309_16913_gb300 import datagen as dg
+    import oracle
+    w = dg.workload(WORKLOAD, seed=1, n=args.n, q=args.q)
+    F = args.fanout or 16
+    t0 = time.perf_counter()
+    tree = oracle.Tree(w.rects, w.ids, F)
+    tb = time.perf_counter() - t0
+    qs = w.queries[:CPU_SAMPLE_QUERIES]
+    for _ in range(args.warmup):
+        tree.select(qs)
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        tree.select(qs)
+    el = time.perf_counter() - t1
+    per_q = el / (args.steps * qs.shape[0])
+    Q = w.queries.shape[0]
+    value = Q / (tb + per_q * Q)
+    cpu = {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"tree built once ({tb:.2f} s); each step = sorted select of the first "
+                     f"{qs.shape[0]} of {Q} queries; value = {Q} / (build + per_query * {Q})"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"scaled range select: {w.rects.shape[0]} rects, {Q} queries",
+                       "fanout": F},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * rtree.h -- C ABI of the GB300 (sm_103a) R-tree library (librtree.so).
+ *
+ * Operations (arXiv 2309.16913, "SIMD-ified R-tree Query Processing and
+ * Optimization"):
+ *   - range select (Section 3): for each query rectangle q, the ids of all
+ *     indexed rectangles r with r INTERSECTS q;
+ *   - R-tree join (Section 4, after Brinkhoff, Kriegel and Seeger 1993): all
+ *     (r_id, s_id) with R_r INTERSECTS S_s, found by traversing both trees
+ *     top-down in step.
+ * INTERSECTS is the closed-interval test on both axes:
+ *     a.xmin <= b.xmax && b.xmin <= a.xmax && a.ymin <= b.ymax && b.ymin <= a.ymax
+ * so rectangles that only touch intersect.  All tests are float32
+ * comparisons; nothing is rounded, so results are exact.
+ *
+ * Data layout.  A rectangle is four float32 values [xmin, ymin, xmax, ymax];
+ * an array of n rectangles is n*4 contiguous floats (16 bytes per row).  Ids
+ * are int32.  Pointers passed in may be device pointers or host pointers
+ * (pageable or pinned); the library tells them apart and copies host inputs
+ * to the device on the given stream (device inputs that are not 16-byte
+ * aligned are copied too).
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Every call below returns only after its device work on that stream
+ * has finished, so results may be read as soon as a call returns RTREE_OK.
+ *
+ * Errors.  Every call returns an rtree_status; on failure no output is
+ * produced (output handles are set to NULL) and rtree_last_error() describes
+ * the failure (per host thread).  No call aborts the process.
+ *
+ * Thread safety.  Distinct trees and results may be used from different host
+ * threads.  A tree may be queried by several threads at once; rtree_free must
+ * not race with queries on the same tree.
+ */
+#ifndef RTREE_H
+#define RTREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RTREE_API __attribute__((visibility("default")))
+#else
+#define RTREE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum rtree_status {
+    RTREE_OK = 0,
+    RTREE_EINVAL = 1,    /* bad argument, NaN coordinate or xmin > xmax / ymin > ymax */
+    RTREE_ENOMEM = 2,    /* a device or host allocation failed */
+    RTREE_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
+    RTREE_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    RTREE_EOVERFLOW = 5, /* a size exceeds a fixed capacity (message says which) */
+    RTREE_EINTERNAL = 6  /* a device-side consistency check failed */
+} rtree_status;
+
+/* Node layouts (Section 2.3).  SOA is layout D1: per node, the F lower-x
+ * values, then F lower-y, F upper-x, F upper-y.  AOS is layout D0: per node,
+ * F entries of 16 bytes each (xmin, ymin, xmax, ymax). */
+enum { RTREE_LAYOUT_SOA = 0, RTREE_LAYOUT_AOS = 1 };
+
+/* How range-select work is spread over the GPU. */
+enum {
+    RTREE_MAP_AUTO = 0,           /* library choice (currently WARP_PER_QUERY) */
+    RTREE_MAP_WARP_PER_QUERY = 1, /* one warp walks one query's whole subtree */
+    RTREE_MAP_WORK_QUEUE = 2      /* persistent warps share (query, node) items through a
+                                     device work queue, so large queries are split */
+};
+
+/* Build configuration.  A zeroed struct (or NULL) selects the defaults. */
+typedef struct rtree_config {
+    int32_t fanout; /* maximum entries per node F: 4, 8, 16, 32, 64 or 128; 0 -> 16 */
+    int32_t layout; /* RTREE_LAYOUT_*; default SOA */
+    int32_t reserved[6];
+} rtree_config_t;
+
+/* Range-select options.  NULL selects the defaults. */
+typedef struct rtree_select_opts {
+    int32_t unsorted; /* 0 (default): ids of each query ascending; 1: traversal order */
+    int32_t mapping;  /* RTREE_MAP_* */
+    int32_t reserved[6];
+} rtree_select_opts_t;
+
+typedef struct rtree rtree_t;               /* opaque; owns device memory */
+typedef struct rtree_result rtree_result_t; /* opaque; owns device memory */
+
+typedef struct rtree_info {
+    int64_t n;            /* indexed rectangles */
+    int64_t nodes;        /* nodes over all levels */
+    int32_t levels;       /* tree height; 0 for an empty tree, 1 if the root is a leaf */
+    int32_t fanout;       /* F */
+    int32_t layout;       /* RTREE_LAYOUT_* */
+    int32_t device;       /* CUDA device holding the tree */
+    int64_t device_bytes; /* device memory held by the tree */
+    float root_mbr[4];    /* bounding box of all rectangles (empty tree: +inf,+inf,-inf,-inf) */
+} rtree_info_t;
+
+/*
+ * rtree_build -- bulk-load an R-tree with Sort-Tile-Recursive packing.
+ *
+ * The paper indexes a main-memory R-tree whose node holds up to F entries
+ * (MBR, ptr) plus depth and count (Section 2.3) but does not say how it is
+ * built.  This call packs it bottom-up with STR: at each level the m items
+ * are sorted by the float32 centre key xmin+xmax (ties by item index), cut
+ * into S = ceil(sqrt(ceil(m/F))) slabs of S*F items, each slab sorted by
+ * ymin+ymax (ties by item index), and runs of F items become nodes; this is
+ * repeated on the node MBRs until one node (the root) remains.  A centre key
+ * that is NaN (-inf + inf) counts as 0 and -0 as +0.
+ *
+ * rects: n*4 floats, ids: n int32 (NULL -> ids 0..n-1); host or device.
+ * n = 0 builds a valid empty tree.  n must be < 2^31.
+ * The inputs are copied; the caller keeps ownership and may free them once
+ * the call returns.  *out receives the tree (free with rtree_free).
+ * Errors: RTREE_EINVAL for a NaN coordinate, xmin > xmax or ymin > ymax in
+ * any row, an unsupported fanout/layout, or NULL out; RTREE_ENOMEM.
+ */
+RTREE_API rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
+                         const rtree_config_t *cfg, void *stream, rtree_t **out);
+
+/* Releases the tree's device memory.  NULL is ignored. */
+RTREE_API void rtree_free(rtree_t *tree);
+
+/* Fills *info.  Errors: RTREE_EINVAL for NULL arguments. */
+RTREE_API rtree_status rtree_get_info(const rtree_t *tree, rtree_info_t *info);
+
+/*
+ * rtree_export -- copy the tree to caller-owned host arrays, level by level
+ * from the root.  Within a level, nodes come in the order their parents list
+ * them; entries keep their packing order.
+ *   level_nodes[levels]       nodes per level, root level first
+ *   counts[nodes]             entries per node
+ *   mbrs[nodes * F * 4]       entry MBRs; unused slots are (+inf,+inf,-inf,-inf)
+ *   leaf_ids[n]               ids of the leaf entries, leaves in export order
+ * Used to compare the device-built tree with an independently built one.
+ */
+RTREE_API rtree_status rtree_export(const rtree_t *tree, int64_t *level_nodes, int32_t *counts,
+                          float *mbrs, int32_t *leaf_ids, void *stream);
+
+/*
+ * rtree_range_select -- batched range select (Section 3).
+ *
+ * For every query i (queries: q*4 floats, host or device) returns the ids of
+ * all indexed rectangles that intersect it, as CSR: offsets[q+1] (int64) and
+ * ids[total] (int32), query i owning ids[offsets[i] .. offsets[i+1]).  Ids of
+ * one query are ascending unless opts->unsorted.  Queries may be degenerate
+ * (points, lines) or infinite.  A query is used as given: the predicate is
+ * evaluated literally, so a query with a NaN coordinate matches nothing and
+ * an inverted query (xmin > xmax) matches whatever the four comparisons
+ * accept; neither is an error.
+ *
+ * The traversal is the paper's vectorized select recast for a warp: a
+ * query's node is tested against all F child MBRs at once (one lane per
+ * child), qualifying children are compacted with a ballot into a per-warp
+ * stack (the queue insertion of step 4), and a child whose MBR lies inside
+ * the query contributes its whole subtree without further tests.  Output is
+ * written in two passes (count, exclusive scan, scatter) and then sorted per
+ * query.
+ *
+ * *out receives the result (free with rtree_result_free), resident on the
+ * tree's device.  Errors: RTREE_EINVAL (NULL tree/out, q < 0), RTREE_ENOMEM,
+ * RTREE_EINTERNAL, RTREE_ECUDA.
+ */
+RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *queries, int64_t q,
+                                const rtree_select_opts_t *opts, void *stream,
+                                rtree_result_t **out);
+
+/*
+ * rtree_range_select_stats -- traversal counters of one count pass over the
+ * same queries (no output is produced).  stats[0..5] receive: queries, nodes
+ * visited, leaf nodes visited, children taken whole because their MBR lies
+ * inside the query, ids found, ids found through such whole children;
+ * stats[6..7] are 0.  Used to turn kernel times into bytes per second.
+ */
+RTREE_API rtree_status rtree_range_select_stats(const rtree_t *tree, const float *queries, int64_t q,
+                                                void *stream, int64_t stats[8]);
+
+/*
+ * rtree_join -- R-tree join (Section 4).
+ *
+ * Returns every pair (r_id, s_id) of rectangles from tree r and tree s that
+ * intersect, sorted lexicographically, as ids[2*total] (int32 pairs).  Both
+ * trees are walked top-down together from their roots, following entry pairs
+ * whose MBRs intersect; where the heights differ, only the taller tree
+ * descends until the heights match.  Each node pair is tested by one warp:
+ * every outer child's MBR is broadcast to all lanes and compared with the
+ * inner children held one per lane (the one-to-many comparison of Section
+ * 4.1).  The trees may have different fanouts and layouts but must be on the
+ * same device.  Errors: RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA.
+ */
+RTREE_API rtree_status rtree_join(const rtree_t *r, const rtree_t *s, void *stream, rtree_result_t **out);
+
+/* Result accessors.  Pointers are device pointers owned by the result. */
+RTREE_API int64_t rtree_result_total(const rtree_result_t *res);         /* ids (select) or pairs (join) */
+RTREE_API int64_t rtree_result_rows(const rtree_result_t *res);          /* q for select, 0 for join */
+RTREE_API const int64_t *rtree_result_offsets(const rtree_result_t *res); /* q+1 entries, NULL for join */
+RTREE_API const int32_t *rtree_result_ids(const rtree_result_t *res);     /* total (select) or 2*total (join) */
+
+/* Copies a result to caller-owned host arrays (offsets may be NULL; sized as
+ * the accessors above say). */
+RTREE_API rtree_status rtree_result_copy_to_host(const rtree_result_t *res, int64_t *offsets,
+                                       int32_t *ids, void *stream);
+
+/* Releases a result.  NULL is ignored. */
+RTREE_API void rtree_result_free(rtree_result_t *res);
+
+/* Description of the last failure on this host thread ("" if none). */
+RTREE_API const char *rtree_last_error(void);
+
+/* Library version string. */
+RTREE_API const char *rtree_version(void);
+
+/*
+ * Kernel accounting.  Every kernel launch the library makes is counted under
+ * a short name ("select_count", "sort_mid", ...).  With timing enabled, CUDA
+ * events recorded on the launching stream bracket each launch and their
+ * elapsed times are summed per name (this adds two event records per
+ * launch).  rtree_timing_get returns 0 past the last name; name strings stay
+ * valid until the library is unloaded.
+ */
+RTREE_API void rtree_timing_enable(int on);
+RTREE_API void rtree_timing_reset(void);
+RTREE_API int rtree_timing_get(int index, const char **name, long long *launches, double *ms);
+RTREE_API long long rtree_launch_count(void);
+
+/* Testing hook: the k-th device allocation after this call fails with
+ * RTREE_ENOMEM (k = 0: the next one); k < 0 disables.  The failure is made
+ * on the host, before cudaMallocAsync is called; no GPU fault is involved. */
+RTREE_API void rtree_debug_fail_alloc_after(long long k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTREE_H */

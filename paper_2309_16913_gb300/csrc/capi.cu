@@ -1,0 +1,462 @@
+// capi.cu -- the extern "C" entry points declared in include/rtree.h.
+//
+// Argument checks, host/device staging of inputs, error reporting and
+// object lifetimes live here; the computation is in build.cu, select.cu,
+// segsort.cu, join.cu, radix_sort.cu and scan.cu.
+#include <atomic>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+namespace rt {
+
+static thread_local std::string g_err;
+static std::atomic<long long> g_alloc_countdown{-1};  // < 0: no injected failure
+
+rtree_status fail(rtree_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+void clear_error() { g_err.clear(); }
+
+static void setup_device_pool(int dev)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64 || done[dev])
+        return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;  // keep freed blocks in the pool between calls
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what)
+{
+    *p = nullptr;
+    long long c = g_alloc_countdown.load();
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 0)
+                return fail(RTREE_ENOMEM, "injected allocation failure (%s, %zu bytes)", what, bytes);
+            break;
+        }
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(RTREE_ENOMEM, "out of device memory: %zu bytes for %s", bytes, what);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(RTREE_ECUDA, "cudaMallocAsync(%zu) for %s: %s", bytes, what, cudaGetErrorString(e));
+    }
+    return RTREE_OK;
+}
+
+void dfree(void *p, cudaStream_t s)
+{
+    if (p)
+        cudaFreeAsync(p, s);
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (dev != prev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+// Where a pointer lives: 1 = device memory usable by kernels, 0 = host.
+int pointer_kind(const void *p, int *device)
+{
+    cudaPointerAttributes a;
+    memset(&a, 0, sizeof(a));
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (device)
+            *device = a.device;
+        return 1;
+    }
+    return 0;
+}
+
+// Returns a 16-byte aligned device copy (or the pointer itself) of n rows.
+template <typename T>
+rtree_status stage(const void *p, size_t bytes, size_t align, cudaStream_t s, DevBuf<T> &tmp,
+                   const T **out)
+{
+    if (bytes == 0) {
+        RT_TRY(tmp.alloc(1, "input staging"));
+        *out = tmp.p;
+        return RTREE_OK;
+    }
+    const bool dev = pointer_kind(p, nullptr) == 1;
+    if (dev && (reinterpret_cast<uintptr_t>(p) % align) == 0) {
+        *out = static_cast<const T *>(p);
+        return RTREE_OK;
+    }
+    RT_TRY(tmp.alloc(bytes / sizeof(T) + 1, "input staging"));
+    RT_CUDA(cudaMemcpyAsync(tmp.p, p, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    *out = tmp.p;
+    return RTREE_OK;
+}
+
+void free_tree_arrays(rtree *t)
+{
+    if (t->mbr)
+        cudaFree(t->mbr);
+    if (t->meta)
+        cudaFree(t->meta);
+    if (t->nbox)
+        cudaFree(t->nbox);
+    if (t->ids)
+        cudaFree(t->ids);
+    t->mbr = nullptr;
+    t->meta = nullptr;
+    t->nbox = nullptr;
+    t->ids = nullptr;
+}
+
+bool fanout_ok(int f) { return f == 4 || f == 8 || f == 16 || f == 32 || f == 64 || f == 128; }
+
+}  // namespace
+}  // namespace rt
+
+using namespace rt;
+
+extern "C" {
+
+const char *rtree_last_error(void) { return g_err.c_str(); }
+
+const char *rtree_version(void) { return "rtree-gb300 0.1 (sm_103a)"; }
+
+// Test hook: make the k-th following device allocation fail (k = -1 disables).
+void rtree_debug_fail_alloc_after(long long k) { g_alloc_countdown.store(k); }
+
+rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
+                         const rtree_config_t *cfg, void *stream, rtree_t **out)
+{
+    clear_error();
+    if (!out)
+        return fail(RTREE_EINVAL, "rtree_build: out is NULL");
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t)INT32_MAX)
+        return fail(RTREE_EINVAL, "rtree_build: n = %lld out of range [0, 2^31-1)", (long long)n);
+    if (n > 0 && !rects)
+        return fail(RTREE_EINVAL, "rtree_build: rects is NULL");
+    const int F = (cfg && cfg->fanout) ? cfg->fanout : 16;
+    const int layout = cfg ? cfg->layout : RTREE_LAYOUT_SOA;
+    if (!fanout_ok(F))
+        return fail(RTREE_EINVAL, "rtree_build: fanout %d not in {4,8,16,32,64,128}", F);
+    if (layout != RTREE_LAYOUT_SOA && layout != RTREE_LAYOUT_AOS)
+        return fail(RTREE_EINVAL, "rtree_build: unknown layout %d", layout);
+    try {
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        int dev = 0;
+        RT_CUDA(cudaGetDevice(&dev));
+        if (n > 0)
+            pointer_kind(rects, &dev);
+        DeviceGuard guard(dev);
+        setup_device_pool(dev);
+        rtree *t = new rtree();
+        t->device = dev;
+        rtree_status st;
+        {
+            DevBuf<float4> rtmp(s);
+            DevBuf<int32_t> itmp(s);
+            const float4 *drects = nullptr;
+            const int32_t *dids = nullptr;
+            st = stage<float4>(rects, (size_t)n * 16, 16, s, rtmp, &drects);
+            if (st == RTREE_OK && ids)
+                st = stage<int32_t>(ids, (size_t)n * 4, 4, s, itmp, &dids);
+            if (st == RTREE_OK)
+                st = build_tree(drects, dids, n, F, layout, s, t);
+            if (st == RTREE_OK) {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess)
+                    st = fail(RTREE_ECUDA, "rtree_build: %s", cudaGetErrorString(e));
+            }
+        }
+        if (st != RTREE_OK) {
+            free_tree_arrays(t);
+            delete t;
+            return st;
+        }
+        timing_resolve();
+        *out = t;
+        return RTREE_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(RTREE_ENOMEM, "rtree_build: host allocation failed");
+    } catch (...) {
+        return fail(RTREE_EINTERNAL, "rtree_build: unexpected exception");
+    }
+}
+
+void rtree_free(rtree_t *t)
+{
+    if (!t)
+        return;
+    DeviceGuard guard(t->device);
+    free_tree_arrays(t);
+    delete t;
+}
+
+rtree_status rtree_get_info(const rtree_t *t, rtree_info_t *info)
+{
+    clear_error();
+    if (!t || !info)
+        return fail(RTREE_EINVAL, "rtree_get_info: NULL argument");
+    info->n = t->n;
+    info->nodes = t->nodes;
+    info->levels = t->levels;
+    info->fanout = t->fanout;
+    info->layout = t->layout;
+    info->device = t->device;
+    info->device_bytes = t->bytes;
+    memcpy(info->root_mbr, t->root_mbr, sizeof(info->root_mbr));
+    return RTREE_OK;
+}
+
+rtree_status rtree_export(const rtree_t *t, int64_t *level_nodes, int32_t *counts, float *mbrs,
+                          int32_t *leaf_ids, void *stream)
+{
+    clear_error();
+    if (!t)
+        return fail(RTREE_EINVAL, "rtree_export: tree is NULL");
+    if (t->levels == 0)
+        return RTREE_OK;
+    if (!level_nodes || !counts || !mbrs || !leaf_ids)
+        return fail(RTREE_EINVAL, "rtree_export: NULL output");
+    try {
+        DeviceGuard guard(t->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int F = t->fanout;
+        const int64_t M = t->nodes;
+        for (int e = 0; e < t->levels; ++e)
+            level_nodes[e] = t->level_nodes[e];
+        int4 *meta = static_cast<int4 *>(malloc(M * sizeof(int4)));
+        float *raw = static_cast<float *>(malloc(M * F * 4 * sizeof(float)));
+        if (!meta || !raw) {
+            free(meta);
+            free(raw);
+            return fail(RTREE_ENOMEM, "rtree_export: host allocation failed");
+        }
+        cudaError_t e1 = cudaMemcpyAsync(meta, t->meta, M * sizeof(int4), cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaMemcpyAsync(raw, t->mbr, M * F * 4 * sizeof(float), cudaMemcpyDeviceToHost, s);
+        cudaError_t e3 = cudaMemcpyAsync(leaf_ids, t->ids, t->n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        cudaError_t e4 = cudaStreamSynchronize(s);
+        if (e1 || e2 || e3 || e4) {
+            free(meta);
+            free(raw);
+            return fail(RTREE_ECUDA, "rtree_export: copy failed: %s",
+                        cudaGetErrorString(e1 ? e1 : e2 ? e2 : e3 ? e3 : e4));
+        }
+        for (int64_t g = 0; g < M; ++g) {
+            counts[g] = meta[g].y;
+            for (int j = 0; j < F; ++j) {
+                float *o = mbrs + (g * F + j) * 4;
+                if (t->layout == RTREE_LAYOUT_AOS) {
+                    memcpy(o, raw + (g * F + j) * 4, 16);
+                } else {
+                    const float *b = raw + g * 4 * F + j;
+                    o[0] = b[0];
+                    o[1] = b[F];
+                    o[2] = b[2 * F];
+                    o[3] = b[3 * F];
+                }
+            }
+        }
+        free(meta);
+        free(raw);
+        return RTREE_OK;
+    } catch (...) {
+        return fail(RTREE_ENOMEM, "rtree_export: host allocation failed");
+    }
+}
+
+rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t q,
+                                const rtree_select_opts_t *opts, void *stream,
+                                rtree_result_t **out)
+{
+    clear_error();
+    if (!out)
+        return fail(RTREE_EINVAL, "rtree_range_select: out is NULL");
+    *out = nullptr;
+    if (!t)
+        return fail(RTREE_EINVAL, "rtree_range_select: tree is NULL");
+    if (q < 0 || q >= (int64_t)INT32_MAX)
+        return fail(RTREE_EINVAL, "rtree_range_select: q = %lld out of range", (long long)q);
+    if (q > 0 && !queries)
+        return fail(RTREE_EINVAL, "rtree_range_select: queries is NULL");
+    const bool sorted = !(opts && opts->unsorted);
+    const int mapping = opts ? opts->mapping : RTREE_MAP_AUTO;
+    if (mapping < RTREE_MAP_AUTO || mapping > RTREE_MAP_WORK_QUEUE)
+        return fail(RTREE_EINVAL, "rtree_range_select: unknown mapping %d", mapping);
+    try {
+        DeviceGuard guard(t->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        rtree_result *res = new rtree_result();
+        res->device = t->device;
+        rtree_status st;
+        {
+            DevBuf<float4> qtmp(s);
+            const float4 *dq = nullptr;
+            st = stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq);
+            if (st == RTREE_OK)
+                st = range_select(t, dq, q, sorted, mapping, s, res);
+            if (st == RTREE_OK) {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess)
+                    st = fail(RTREE_ECUDA, "rtree_range_select: %s", cudaGetErrorString(e));
+            }
+        }
+        if (st != RTREE_OK) {
+            if (res->offsets)
+                cudaFree(res->offsets);
+            if (res->ids)
+                cudaFree(res->ids);
+            delete res;
+            return st;
+        }
+        timing_resolve();
+        *out = res;
+        return RTREE_OK;
+    } catch (...) {
+        return fail(RTREE_ENOMEM, "rtree_range_select: host allocation failed");
+    }
+}
+
+rtree_status rtree_range_select_stats(const rtree_t *t, const float *queries, int64_t q, void *stream,
+                                      int64_t stats[8])
+{
+    clear_error();
+    if (!t || !stats || q < 0 || (q > 0 && !queries))
+        return fail(RTREE_EINVAL, "rtree_range_select_stats: bad argument");
+    try {
+        DeviceGuard guard(t->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DevBuf<float4> qtmp(s);
+        const float4 *dq = nullptr;
+        RT_TRY(stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq));
+        RT_TRY(select_stats(t, dq, q, s, stats));
+        RT_CUDA(cudaStreamSynchronize(s));
+        timing_resolve();
+        return RTREE_OK;
+    } catch (...) {
+        return fail(RTREE_ENOMEM, "rtree_range_select_stats: host allocation failed");
+    }
+}
+
+rtree_status rtree_join(const rtree_t *r, const rtree_t *s_tree, void *stream, rtree_result_t **out)
+{
+    clear_error();
+    if (!out)
+        return fail(RTREE_EINVAL, "rtree_join: out is NULL");
+    *out = nullptr;
+    if (!r || !s_tree)
+        return fail(RTREE_EINVAL, "rtree_join: tree is NULL");
+    if (r->device != s_tree->device)
+        return fail(RTREE_EINVAL, "rtree_join: trees on devices %d and %d", r->device, s_tree->device);
+    try {
+        DeviceGuard guard(r->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        rtree_result *res = new rtree_result();
+        res->device = r->device;
+        rtree_status st = tree_join(r, s_tree, s, res);
+        if (st == RTREE_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess)
+                st = fail(RTREE_ECUDA, "rtree_join: %s", cudaGetErrorString(e));
+        }
+        if (st != RTREE_OK) {
+            if (res->ids)
+                cudaFree(res->ids);
+            delete res;
+            return st;
+        }
+        timing_resolve();
+        *out = res;
+        return RTREE_OK;
+    } catch (...) {
+        return fail(RTREE_ENOMEM, "rtree_join: host allocation failed");
+    }
+}
+
+int64_t rtree_result_total(const rtree_result_t *r) { return r ? r->total : 0; }
+int64_t rtree_result_rows(const rtree_result_t *r) { return r ? r->rows : 0; }
+const int64_t *rtree_result_offsets(const rtree_result_t *r) { return r ? r->offsets : nullptr; }
+const int32_t *rtree_result_ids(const rtree_result_t *r) { return r ? r->ids : nullptr; }
+
+rtree_status rtree_result_copy_to_host(const rtree_result_t *r, int64_t *offsets, int32_t *ids,
+                                       void *stream)
+{
+    clear_error();
+    if (!r)
+        return fail(RTREE_EINVAL, "rtree_result_copy_to_host: result is NULL");
+    DeviceGuard guard(r->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (offsets && r->offsets)
+        RT_CUDA(cudaMemcpyAsync(offsets, r->offsets, (r->rows + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+    const int64_t nids = r->offsets ? r->total : 2 * r->total;
+    if (ids && nids > 0)
+        RT_CUDA(cudaMemcpyAsync(ids, r->ids, nids * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    return RTREE_OK;
+}
+
+void rtree_result_free(rtree_result_t *r)
+{
+    if (!r)
+        return;
+    DeviceGuard guard(r->device);
+    if (r->offsets)
+        cudaFree(r->offsets);
+    if (r->ids)
+        cudaFree(r->ids);
+    delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// internal.cuh -- shared declarations of the R-tree CUDA library (not public).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "rtree.h"
+
+#define RT_FULL 0xffffffffu
+#define RT_MAX_LEVELS 40
+
+namespace rt {
+
+// ------------------------------------------------------------------ errors
+// Records a thread-local message and returns st.
+rtree_status fail(rtree_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+void clear_error();
+
+#define RT_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::rt::fail(RTREE_ECUDA, "%s failed: %s (%s:%d)", #call,                 \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+    } while (0)
+#define RT_LAUNCH() RT_CUDA(cudaGetLastError())
+#define RT_TRY(x)                                                                          \
+    do {                                                                                   \
+        rtree_status s_ = (x);                                                             \
+        if (s_ != RTREE_OK)                                                                \
+            return s_;                                                                     \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+// Device memory from the stream-ordered pool of the current device.  A
+// host-side counter can make the k-th allocation fail (fault injection for
+// tests; no GPU fault is involved).
+rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what);
+void dfree(void *p, cudaStream_t s);
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    explicit DevBuf(cudaStream_t st) : s(st) {}
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    rtree_status alloc(size_t n, const char *what)
+    {
+        reset();
+        return dmalloc(reinterpret_cast<void **>(&p), (n ? n : 1) * sizeof(T), s, what);
+    }
+    void reset()
+    {
+        if (p) {
+            dfree(p, s);
+            p = nullptr;
+        }
+    }
+    T *release()
+    {
+        T *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+int sm_count();
+
+// Counts a kernel launch under `name` and, when timing is enabled, records
+// CUDA events around it on stream s.  Scope it around the launch.
+class KernelTimer {
+  public:
+    KernelTimer(const char *name, cudaStream_t s);
+    ~KernelTimer();
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    cudaStream_t s_;
+    int entry_ = 0;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+// Resolves recorded event pairs into totals (call after a stream sync).
+void timing_resolve();
+
+// -------------------------------------------------------------------- tree
+// Device view of a tree.  Nodes of all levels are numbered level by level
+// from the root (node 0); leaves are the last level.
+//   mbr : entry MBRs.  SOA: node g owns floats [g*4F, g*4F+4F): F lower-x,
+//         F lower-y, F upper-x, F upper-y.  AOS: node g owns float4 slots
+//         [g*F, g*F+F).  Unused slots hold (+inf, +inf, -inf, -inf).
+//   meta: per node {first, count, elo, ehi}: first = global index of the
+//         first child (internal) or index of the first entry in ids (leaf);
+//         [elo, ehi) = the ids of all entries under the node.
+//   nbox: per node, its bounding box (equal to its entry in the parent).
+//   ids : entry ids, leaves in node order, entries in slot order.
+struct TreeDev {
+    const float *mbr;
+    const int4 *meta;
+    const float4 *nbox;
+    const int32_t *ids;
+    int32_t leaf_base;
+    int32_t nodes;
+    int32_t levels;
+    int32_t fanout;
+    int32_t layout;
+};
+
+}  // namespace rt
+
+struct rtree {
+    int device = 0;
+    int32_t fanout = 16;
+    int32_t layout = RTREE_LAYOUT_SOA;
+    int32_t levels = 0;
+    int64_t n = 0;
+    int64_t nodes = 0;
+    int64_t level_nodes[RT_MAX_LEVELS] = {};  // root level first
+    int64_t level_base[RT_MAX_LEVELS] = {};
+    float *mbr = nullptr;
+    int4 *meta = nullptr;
+    float4 *nbox = nullptr;
+    int32_t *ids = nullptr;
+    float root_mbr[4] = {0, 0, 0, 0};
+    int64_t bytes = 0;
+
+    rt::TreeDev view() const
+    {
+        rt::TreeDev v;
+        v.mbr = mbr;
+        v.meta = meta;
+        v.nbox = nbox;
+        v.ids = ids;
+        v.leaf_base = levels ? (int32_t)level_base[levels - 1] : 0;
+        v.nodes = (int32_t)nodes;
+        v.levels = levels;
+        v.fanout = fanout;
+        v.layout = layout;
+        return v;
+    }
+};
+
+struct rtree_result {
+    int device = 0;
+    int64_t rows = 0;   // queries (select) or 0 (join)
+    int64_t total = 0;  // ids (select) or pairs (join)
+    int64_t *offsets = nullptr;
+    int32_t *ids = nullptr;
+};
+
+namespace rt {
+
+// ------------------------------------------------------- device primitives
+// Closed-interval intersection of two boxes (x=xmin, y=ymin, z=xmax, w=ymax).
+__device__ __forceinline__ bool meets(float4 a, float4 b)
+{
+    return a.x <= b.z && b.x <= a.z && a.y <= b.w && b.y <= a.w;
+}
+
+// c lies inside q (every rectangle inside c then meets q).
+__device__ __forceinline__ bool inside(float4 c, float4 q)
+{
+    return q.x <= c.x && c.z <= q.z && q.y <= c.y && c.w <= q.w;
+}
+
+__device__ __forceinline__ float4 empty_box()
+{
+    return make_float4(__int_as_float(0x7f800000), __int_as_float(0x7f800000),
+                       __int_as_float(0xff800000), __int_as_float(0xff800000));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Child box j of node g.
+__device__ __forceinline__ float4 load_entry(const float *__restrict__ mbr, int layout, int F,
+                                             int64_t g, int j)
+{
+    if (layout == RTREE_LAYOUT_AOS)
+        return __ldg(reinterpret_cast<const float4 *>(mbr) + g * F + j);
+    const float *b = mbr + g * 4 * F + j;
+    return make_float4(__ldg(b), __ldg(b + F), __ldg(b + 2 * F), __ldg(b + 3 * F));
+}
+
+template <int F, int LAYOUT>
+__device__ __forceinline__ float4 load_entry_t(const float *__restrict__ mbr, int64_t g, int j)
+{
+    if (LAYOUT == RTREE_LAYOUT_AOS)
+        return __ldg(reinterpret_cast<const float4 *>(mbr) + g * F + j);
+    const float *b = mbr + g * 4 * F + j;
+    return make_float4(__ldg(b), __ldg(b + F), __ldg(b + 2 * F), __ldg(b + 3 * F));
+}
+
+// ------------------------------------------------------ host-side helpers
+// Exclusive scan; out has n+1 entries and out[n] is the total.
+rtree_status scan_exclusive(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+rtree_status scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+rtree_status scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).
+// Inputs are not modified; outputs must not alias inputs.
+rtree_status radix_sort_pairs(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
+                              uint32_t *vout, int64_t n, int bit_lo, int bit_hi, cudaStream_t s);
+
+// Sorts every segment ids[offsets[i] .. offsets[i+1]) ascending (signed).
+rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
+                            cudaStream_t s);
+
+// Builds the tree from device rectangles (float4 rows) and device ids (or NULL).
+rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int fanout, int layout,
+                        cudaStream_t s, rtree *t);
+
+// Range select for device queries (float4 rows).
+rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,
+                          int mapping, cudaStream_t s, rtree_result *res);
+
+// Traversal statistics of one count pass (see rtree_range_select_stats).
+rtree_status select_stats(const rtree *t, const float4 *queries, int64_t q, cudaStream_t s,
+                          int64_t out[8]);
+
+// R-tree join of two trees on the same device.
+rtree_status tree_join(const rtree *r, const rtree *s_tree, cudaStream_t s, rtree_result *res);
+
+}  // namespace rt

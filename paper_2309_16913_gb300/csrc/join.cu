@@ -1,0 +1,243 @@
+// join.cu -- R-tree join (Section 4), synchronized top-down traversal.
+//
+// Both trees are walked from their roots together (Brinkhoff, Kriegel and
+// Seeger 1993): a node pair (a, b) whose entries intersect yields child
+// pairs, and leaf pairs yield (r_id, s_id).  The frontier is processed one
+// level at a time; every node pair is tested by one warp with the
+// one-to-many comparison of Section 4.1: the inner node's children sit one
+// per lane (G = min(32, F_s) lanes per outer child, so 32/G outer children
+// are tested per step), each outer child's MBR is broadcast to its lanes,
+// and __ballot_sync over the four comparisons gives the qualifying inner
+// children, compacted with popc(mask & lanemask_lt) (queue insertion, step 4).
+// Where the heights differ, only the taller tree descends: its children are
+// tested against the other node's bounding box.
+//
+// Output is written in two passes per level (count, scan, scatter).  The
+// final (r_id, s_id) pairs are sorted lexicographically by two stable radix
+// sorts (by s, then by r).
+#include "internal.cuh"
+
+namespace rt {
+namespace {
+
+enum { J_BOTH = 0, J_A = 1, J_B = 2, J_LEAF = 3 };
+enum { PASS_COUNT = 0, PASS_SCATTER = 1 };
+constexpr int kThreads = 256;
+constexpr uint32_t kSign = 0x80000000u;
+
+template <int MODE, int PASS>
+__global__ void __launch_bounds__(kThreads)
+    k_join(TreeDev ta, TreeDev tb, const int2 *__restrict__ pairs, int64_t np,
+           int32_t *__restrict__ counts, const int64_t *__restrict__ offs, int2 *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int Fa = ta.fanout, Fb = tb.fanout;
+    for (int64_t p = warp; p < np; p += nwarps) {
+        const int2 pr = pairs[p];
+        const int a = pr.x, b = pr.y;
+        const int4 ma = __ldg(ta.meta + a), mb = __ldg(tb.meta + b);
+        int64_t base = 0;
+        if (PASS == PASS_SCATTER)
+            base = offs[p];
+        int cur = 0;
+        if (MODE == J_A) {
+            const float4 bb = __ldg(tb.nbox + b);
+            for (int i0 = 0; i0 < ma.y; i0 += 32) {
+                const int i = i0 + lane;
+                const bool hit = i < ma.y && meets(load_entry(ta.mbr, ta.layout, Fa, a, i), bb);
+                const unsigned m = __ballot_sync(RT_FULL, hit);
+                if (PASS == PASS_SCATTER && hit)
+                    out[base + cur + __popc(m & lt)] = make_int2(ma.x + i, b);
+                cur += __popc(m);
+            }
+        } else if (MODE == J_B) {
+            const float4 ab = __ldg(ta.nbox + a);
+            for (int j0 = 0; j0 < mb.y; j0 += 32) {
+                const int j = j0 + lane;
+                const bool hit = j < mb.y && meets(ab, load_entry(tb.mbr, tb.layout, Fb, b, j));
+                const unsigned m = __ballot_sync(RT_FULL, hit);
+                if (PASS == PASS_SCATTER && hit)
+                    out[base + cur + __popc(m & lt)] = make_int2(a, mb.x + j);
+                cur += __popc(m);
+            }
+        } else {
+            const int G = Fb < 32 ? Fb : 32;
+            const int KO = 32 / G;
+            const int grp = lane / G, sub = lane % G;
+            for (int j0 = 0; j0 < mb.y; j0 += G) {
+                const int j = j0 + sub;
+                const bool vj = j < mb.y;
+                const float4 ib = vj ? load_entry(tb.mbr, tb.layout, Fb, b, j) : empty_box();
+                for (int i0 = 0; i0 < ma.y; i0 += KO) {
+                    const int i = i0 + grp;
+                    const bool vi = i < ma.y;
+                    const float4 ob = vi ? load_entry(ta.mbr, ta.layout, Fa, a, i) : empty_box();
+                    const bool hit = vi && vj && meets(ob, ib);
+                    const unsigned m = __ballot_sync(RT_FULL, hit);
+                    if (PASS == PASS_SCATTER && hit) {
+                        int2 v;
+                        if (MODE == J_LEAF)
+                            v = make_int2(__ldg(ta.ids + ma.x + i), __ldg(tb.ids + mb.x + j));
+                        else
+                            v = make_int2(ma.x + i, mb.x + j);
+                        out[base + cur + __popc(m & lt)] = v;
+                    }
+                    cur += __popc(m);
+                }
+            }
+        }
+        if (PASS == PASS_COUNT && lane == 0)
+            counts[p] = cur;
+    }
+}
+
+using JoinKernel = void (*)(TreeDev, TreeDev, const int2 *, int64_t, int32_t *, const int64_t *,
+                            int2 *);
+
+JoinKernel pick(int mode, int pass)
+{
+    switch (mode) {
+    case J_BOTH: return pass == PASS_COUNT ? k_join<J_BOTH, PASS_COUNT> : k_join<J_BOTH, PASS_SCATTER>;
+    case J_A: return pass == PASS_COUNT ? k_join<J_A, PASS_COUNT> : k_join<J_A, PASS_SCATTER>;
+    case J_B: return pass == PASS_COUNT ? k_join<J_B, PASS_COUNT> : k_join<J_B, PASS_SCATTER>;
+    default: return pass == PASS_COUNT ? k_join<J_LEAF, PASS_COUNT> : k_join<J_LEAF, PASS_SCATTER>;
+    }
+}
+
+unsigned grid_for(int64_t np)
+{
+    int64_t g = (np * 32 + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (g > cap)
+        g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+__global__ void k_split_pairs(const int2 *__restrict__ p, int64_t n, uint32_t *__restrict__ key,
+                              uint32_t *__restrict__ val)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 v = p[i];
+        key[i] = (uint32_t)v.y ^ kSign;  // s first (least significant)
+        val[i] = (uint32_t)v.x;
+    }
+}
+
+__global__ void k_flip(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] ^ kSign;
+}
+
+__global__ void k_merge_pairs(const uint32_t *__restrict__ r, const uint32_t *__restrict__ s,
+                              int64_t n, int2 *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_int2((int)(r[i] ^ kSign), (int)(s[i] ^ kSign));
+}
+
+unsigned blocks_for(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 65536 ? 65536 : b));
+}
+
+// Sorts (r, s) pairs lexicographically: stable sort by s, then by r.
+rtree_status sort_pairs(int2 *pairs, int64_t n, cudaStream_t s)
+{
+    if (n <= 1)
+        return RTREE_OK;
+    DevBuf<uint32_t> k0(s), v0(s), k1(s), v1(s);
+    RT_TRY(k0.alloc(n, "join sort"));
+    RT_TRY(v0.alloc(n, "join sort"));
+    RT_TRY(k1.alloc(n, "join sort"));
+    RT_TRY(v1.alloc(n, "join sort"));
+    {
+        KernelTimer kt_("split_pairs", s);
+        k_split_pairs<<<blocks_for(n), 256, 0, s>>>(pairs, n, k0.p, v0.p);
+        RT_LAUNCH();
+    }
+    RT_TRY(radix_sort_pairs(k0.p, v0.p, k1.p, v1.p, n, 0, 32, s));  // by s; v1 = r
+    {
+        KernelTimer kt_("flip", s);
+        k_flip<<<blocks_for(n), 256, 0, s>>>(v1.p, n, k0.p);  // r keys
+        RT_LAUNCH();
+    }
+    RT_TRY(radix_sort_pairs(k0.p, k1.p, v0.p, v1.p, n, 0, 32, s));  // by r; v1 = s keys
+    {
+        KernelTimer kt_("merge_pairs", s);
+        k_merge_pairs<<<blocks_for(n), 256, 0, s>>>(v0.p, v1.p, n, pairs);
+        RT_LAUNCH();
+    }
+    return RTREE_OK;
+}
+
+}  // namespace
+
+rtree_status tree_join(const rtree *R, const rtree *S, cudaStream_t s, rtree_result *res)
+{
+    res->rows = 0;
+    res->total = 0;
+    res->offsets = nullptr;
+    if (R->nodes == 0 || S->nodes == 0) {
+        DevBuf<int32_t> ids(s);
+        RT_TRY(ids.alloc(2, "join pairs"));
+        RT_CUDA(cudaStreamSynchronize(s));
+        res->ids = ids.release();
+        return RTREE_OK;
+    }
+    const TreeDev ta = R->view(), tb = S->view();
+    DevBuf<int2> front(s);
+    RT_TRY(front.alloc(1, "join frontier"));
+    const int2 root = make_int2(0, 0);
+    RT_CUDA(cudaMemcpyAsync(front.p, &root, sizeof(int2), cudaMemcpyHostToDevice, s));
+    int64_t np = 1;
+    int da = 0, db = 0;
+    for (;;) {
+        const int ra = R->levels - 1 - da, rb = S->levels - 1 - db;
+        const int mode = (ra == 0 && rb == 0) ? J_LEAF : (ra > rb ? J_A : (rb > ra ? J_B : J_BOTH));
+        DevBuf<int32_t> cnt(s);
+        DevBuf<int64_t> off(s);
+        RT_TRY(cnt.alloc(np, "join counts"));
+        RT_TRY(off.alloc(np + 1, "join offsets"));
+        {
+            KernelTimer kt_("join_count", s);
+            pick(mode, PASS_COUNT)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np, cnt.p,
+                                                                     nullptr, nullptr);
+            RT_LAUNCH();
+        }
+        RT_TRY(scan_exclusive(cnt.p, off.p, np, s));
+        int64_t total = 0;
+        RT_CUDA(cudaMemcpyAsync(&total, off.p + np, sizeof(total), cudaMemcpyDeviceToHost, s));
+        RT_CUDA(cudaStreamSynchronize(s));
+        DevBuf<int2> next(s);
+        RT_TRY(next.alloc(total, mode == J_LEAF ? "join pairs" : "join frontier"));
+        if (total > 0) {
+            KernelTimer kt_("join_scatter", s);
+            pick(mode, PASS_SCATTER)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np,
+                                                                       nullptr, off.p, next.p);
+            RT_LAUNCH();
+        }
+        if (mode == J_LEAF || total == 0) {
+            RT_TRY(sort_pairs(next.p, total, s));
+            RT_CUDA(cudaStreamSynchronize(s));
+            res->total = total;
+            res->ids = reinterpret_cast<int32_t *>(next.release());
+            return RTREE_OK;
+        }
+        if (mode == J_A || mode == J_BOTH)
+            ++da;
+        if (mode == J_B || mode == J_BOTH)
+            ++db;
+        std::swap(front.p, next.p);
+        np = total;
+    }
+}
+
+}  // namespace rt

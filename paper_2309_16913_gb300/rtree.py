@@ -1,0 +1,397 @@
+"""ctypes binding of the R-tree CUDA library (``include/rtree.h``).
+
+Argument marshalling only: every step of build, select and join runs in the
+library's CUDA kernels.  Functions carry the C names (``rtree_build``,
+``rtree_range_select``, ``rtree_join``, ...); :class:`RTree` and
+:class:`Result` wrap them with ownership.  If ``librtree.so`` has not been
+built this module raises; there is no CPU fallback.
+
+Arrays may be NumPy arrays (host memory) or torch tensors (host or CUDA);
+the library copies host inputs to the device itself.  Streams: ``None``
+means torch's current CUDA stream (or the legacy default stream when torch
+has no CUDA), an ``int`` is a raw ``cudaStream_t``, and a
+``torch.cuda.Stream`` is used as is.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librtree.so")
+
+RTREE_OK, RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA, RTREE_ETIMEOUT, RTREE_EOVERFLOW, RTREE_EINTERNAL = range(7)
+STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_ECUDA",
+                4: "RTREE_ETIMEOUT", 5: "RTREE_EOVERFLOW", 6: "RTREE_EINTERNAL"}
+LAYOUTS = {"soa": 0, "aos": 1}
+MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
+
+
+class RTreeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class rtree_config_t(C.Structure):
+    _fields_ = [("fanout", C.c_int32), ("layout", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class rtree_select_opts_t(C.Structure):
+    _fields_ = [("unsorted", C.c_int32), ("mapping", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class rtree_info_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("levels", C.c_int32),
+                ("fanout", C.c_int32), ("layout", C.c_int32), ("device", C.c_int32),
+                ("device_bytes", C.c_int64), ("root_mbr", C.c_float * 4)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _bind(lib):
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    sigs = {
+        "rtree_build": (C.c_int, [vp, vp, i64, C.POINTER(rtree_config_t), vp, C.POINTER(vp)]),
+        "rtree_free": (None, [vp]),
+        "rtree_get_info": (C.c_int, [vp, C.POINTER(rtree_info_t)]),
+        "rtree_export": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
+        "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
+        "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
+        "rtree_result_total": (i64, [vp]),
+        "rtree_result_rows": (i64, [vp]),
+        "rtree_result_offsets": (vp, [vp]),
+        "rtree_result_ids": (vp, [vp]),
+        "rtree_result_copy_to_host": (C.c_int, [vp, vp, vp, vp]),
+        "rtree_result_free": (None, [vp]),
+        "rtree_last_error": (C.c_char_p, []),
+        "rtree_version": (C.c_char_p, []),
+        "rtree_debug_fail_alloc_after": (None, [C.c_longlong]),
+        "rtree_timing_enable": (None, [C.c_int]),
+        "rtree_timing_reset": (None, []),
+        "rtree_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
+                                       C.POINTER(C.c_double)]),
+        "rtree_launch_count": (C.c_longlong, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def load_library(path: str | None = None):
+    """Loads ``librtree.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library not built ({p} missing); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = _bind(C.CDLL(p))
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(status: int, lib=None):
+    if status != RTREE_OK:
+        lib = lib or load_library()
+        raise RTreeError(status, (lib.rtree_last_error() or b"").decode())
+
+
+# ------------------------------------------------------------- marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _as_rows(x, what: str):
+    """Returns (pointer, rows, keepalive) for an [n, 4] float32 array."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32:
+            raise TypeError(f"{what} must be float32")
+        x = x.reshape(-1, 4)
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x.data_ptr() or None, x.shape[0], x
+    a = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 4)
+    return a.ctypes.data or None, a.shape[0], a
+
+
+def _as_ids(x, n: int):
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.int32:
+            raise TypeError("ids must be int32")
+        x = x.reshape(-1).contiguous()
+        if x.numel() != n:
+            raise ValueError("ids must have one entry per rectangle")
+        return x.data_ptr() or None, x
+    a = np.ascontiguousarray(x, dtype=np.int32).reshape(-1)
+    if a.size != n:
+        raise ValueError("ids must have one entry per rectangle")
+    return a.ctypes.data or None, a
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------- C names, thin wrappers
+def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None) -> int:
+    """Builds a tree; returns the opaque handle (free with rtree_free)."""
+    lib = load_library()
+    rp, n, keep_r = _as_rows(rects, "rects")
+    ip, keep_i = _as_ids(ids, n)
+    cfg = rtree_config_t()
+    cfg.fanout = int(fanout)
+    cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    out = C.c_void_p()
+    _check(lib.rtree_build(rp, ip, n, C.byref(cfg), _stream(stream), C.byref(out)), lib)
+    del keep_r, keep_i
+    return out.value
+
+
+def rtree_free(handle: int) -> None:
+    if handle:
+        load_library().rtree_free(handle)
+
+
+def rtree_get_info(handle: int) -> dict:
+    lib = load_library()
+    info = rtree_info_t()
+    _check(lib.rtree_get_info(handle, C.byref(info)), lib)
+    return {"n": info.n, "nodes": info.nodes, "levels": info.levels, "fanout": info.fanout,
+            "layout": info.layout, "device": info.device, "device_bytes": info.device_bytes,
+            "root_mbr": np.array(info.root_mbr[:], dtype=np.float32)}
+
+
+def rtree_export(handle: int, stream=None) -> dict:
+    lib = load_library()
+    info = rtree_get_info(handle)
+    L, M, F, n = info["levels"], info["nodes"], info["fanout"], info["n"]
+    level_nodes = np.zeros(L, np.int64)
+    counts = np.zeros(M, np.int32)
+    mbrs = np.zeros((M, F, 4), np.float32)
+    leaf_ids = np.zeros(n, np.int32)
+    if L:
+        _check(lib.rtree_export(handle, level_nodes.ctypes.data, counts.ctypes.data,
+                                mbrs.ctypes.data, leaf_ids.ctypes.data, _stream(stream)), lib)
+    return {"level_nodes": level_nodes, "counts": counts, "mbrs": mbrs, "leaf_ids": leaf_ids}
+
+
+def rtree_range_select(handle: int, queries, unsorted: bool = False, mapping: str | int = "auto",
+                       stream=None) -> int:
+    """Runs a batched range select; returns the result handle."""
+    lib = load_library()
+    qp, q, keep = _as_rows(queries, "queries")
+    opts = rtree_select_opts_t()
+    opts.unsorted = 1 if unsorted else 0
+    opts.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
+    out = C.c_void_p()
+    _check(lib.rtree_range_select(handle, qp, q, C.byref(opts), _stream(stream), C.byref(out)), lib)
+    del keep
+    return out.value
+
+
+def rtree_range_select_stats(handle: int, queries, stream=None) -> dict:
+    """Traversal counters of one count pass (no output produced)."""
+    lib = load_library()
+    qp, q, keep = _as_rows(queries, "queries")
+    st = (C.c_int64 * 8)()
+    _check(lib.rtree_range_select_stats(handle, qp, q, _stream(stream), st), lib)
+    del keep
+    keys = ("queries", "nodes_visited", "leaves_visited", "whole_children", "ids", "ids_from_whole")
+    return {k: int(st[i]) for i, k in enumerate(keys)}
+
+
+def rtree_join(r_handle: int, s_handle: int, stream=None) -> int:
+    lib = load_library()
+    out = C.c_void_p()
+    _check(lib.rtree_join(r_handle, s_handle, _stream(stream), C.byref(out)), lib)
+    return out.value
+
+
+def rtree_result_total(res: int) -> int:
+    return load_library().rtree_result_total(res)
+
+
+def rtree_result_rows(res: int) -> int:
+    return load_library().rtree_result_rows(res)
+
+
+def rtree_result_offsets(res: int) -> int:
+    return load_library().rtree_result_offsets(res) or 0
+
+
+def rtree_result_ids(res: int) -> int:
+    return load_library().rtree_result_ids(res) or 0
+
+
+def rtree_result_copy_to_host(res: int, stream=None):
+    """Returns (offsets int64[rows+1] or None, ids int32[...]) as NumPy arrays."""
+    lib = load_library()
+    total, rows = lib.rtree_result_total(res), lib.rtree_result_rows(res)
+    is_join = not lib.rtree_result_offsets(res)
+    offsets = None if is_join else np.zeros(rows + 1, np.int64)
+    ids = np.zeros(2 * total if is_join else total, np.int32)
+    _check(lib.rtree_result_copy_to_host(res, None if offsets is None else offsets.ctypes.data,
+                                         ids.ctypes.data if ids.size else None, _stream(stream)), lib)
+    return offsets, (ids.reshape(-1, 2) if is_join else ids)
+
+
+def rtree_result_free(res: int) -> None:
+    if res:
+        load_library().rtree_result_free(res)
+
+
+def rtree_last_error() -> str:
+    return (load_library().rtree_last_error() or b"").decode()
+
+
+def rtree_version() -> str:
+    return load_library().rtree_version().decode()
+
+
+def rtree_debug_fail_alloc_after(k: int) -> None:
+    load_library().rtree_debug_fail_alloc_after(int(k))
+
+
+def rtree_timing_enable(on: bool = True) -> None:
+    load_library().rtree_timing_enable(1 if on else 0)
+
+
+def rtree_timing_reset() -> None:
+    load_library().rtree_timing_reset()
+
+
+def rtree_timing_get() -> dict:
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    lib = load_library()
+    out, i = {}, 0
+    name, launches, ms = C.c_char_p(), C.c_longlong(), C.c_double()
+    while lib.rtree_timing_get(i, C.byref(name), C.byref(launches), C.byref(ms)):
+        out[name.value.decode()] = (launches.value, ms.value)
+        i += 1
+    return out
+
+
+def rtree_launch_count() -> int:
+    return load_library().rtree_launch_count()
+
+
+# ------------------------------------------------------------ convenience
+class _DeviceArray:
+    """Exposes a library-owned device array through __cuda_array_interface__."""
+
+    def __init__(self, owner, ptr: int, shape: tuple, typestr: str):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class Result:
+    """A select (CSR) or join (pairs) result resident on the device."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            rtree_result_free(h)
+
+    @property
+    def total(self) -> int:
+        return rtree_result_total(self.handle)
+
+    @property
+    def rows(self) -> int:
+        return rtree_result_rows(self.handle)
+
+    @property
+    def is_join(self) -> bool:
+        return rtree_result_offsets(self.handle) == 0
+
+    def to_numpy(self, stream=None):
+        """(offsets, ids) for select; (None, pairs[total, 2]) for join."""
+        return rtree_result_copy_to_host(self.handle, stream)
+
+    def offsets_tensor(self):
+        """Zero-copy torch view of the offsets (keeps this result alive)."""
+        import torch
+        ptr = rtree_result_offsets(self.handle)
+        return torch.as_tensor(_DeviceArray(self, ptr, (self.rows + 1,), "<i8"), device="cuda")
+
+    def ids_tensor(self):
+        """Zero-copy torch view of the ids (select) or pairs (join)."""
+        import torch
+        ptr = rtree_result_ids(self.handle)
+        shape = (self.total, 2) if self.is_join else (self.total,)
+        if self.total == 0:
+            return torch.zeros(shape, dtype=torch.int32, device="cuda")
+        return torch.as_tensor(_DeviceArray(self, ptr, shape, "<i4"), device="cuda")
+
+
+class RTree:
+    """An R-tree on the GPU: build, range select, join."""
+
+    def __init__(self, rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None):
+        self.handle = None
+        self.handle = rtree_build(rects, ids, fanout, layout, stream)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            rtree_free(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        return rtree_get_info(self.handle)
+
+    def export(self, stream=None) -> dict:
+        return rtree_export(self.handle, stream)
+
+    def range_select(self, queries, unsorted: bool = False, mapping="auto", stream=None) -> Result:
+        return Result(rtree_range_select(self.handle, queries, unsorted, mapping, stream))
+
+    def select_stats(self, queries, stream=None) -> dict:
+        return rtree_range_select_stats(self.handle, queries, stream)
+
+    def join(self, other: "RTree", stream=None) -> Result:
+        return Result(rtree_join(self.handle, other.handle, stream))

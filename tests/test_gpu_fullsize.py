@@ -1,0 +1,88 @@
+"""Full-size parity at the benchmark's workloads, in the benchmark's launch
+configuration (the same C ABI calls bench.py times).
+
+The oracle cannot walk a million queries in seconds, so at 10M rectangles
+every query is checked for properties that hold at any size (offsets are a
+valid CSR, each id list strictly ascending and within the id range, the sum
+of counts equals the total) and a seeded sample of queries, including every
+heavy query of the uneven mix, is compared exactly with the oracle.  The
+2M x 2M join is compared in full.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import gpu_ready
+from paper_2309_16913_gb300 import datagen as dg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    return gpu_ready()
+
+
+def check_sample(rt, t_gpu, t_orc, queries, sample, F):
+    import torch
+    q = torch.from_numpy(queries).cuda()
+    res = t_gpu.range_select(q)
+    try:
+        off = res.offsets_tensor().cpu().numpy()
+        ids_dev = res.ids_tensor()
+        assert off[0] == 0 and np.all(np.diff(off) >= 0) and off[-1] == res.total
+        # strictly ascending inside every segment (ids are unique here)
+        d = ids_dev[1:] - ids_dev[:-1]
+        bounds = torch.from_numpy(off[1:-1]).cuda()
+        ok = d > 0
+        if bounds.numel():
+            ok[(bounds - 1)[(bounds > 0) & (bounds < res.total)]] = True
+        assert bool(ok.all()), "segment not strictly ascending"
+        assert int(ids_dev.min()) >= 0 and int(ids_dev.max()) < t_gpu.info()["n"]
+        o_off, o_ids = t_orc.select(queries[sample])
+        for k, qi in enumerate(sample):
+            got = ids_dev[off[qi]:off[qi + 1]].cpu().numpy()
+            assert np.array_equal(got, o_ids[o_off[k]:o_off[k + 1]]), f"query {qi} F={F}"
+        return int(off[-1])
+    finally:
+        res.close()
+
+
+@pytest.mark.parametrize("F", [16, 32, 64])
+def test_scaled_10m_1m_queries(rt, F):
+    import torch
+    w = dg.workload("scaled")
+    t_orc = oracle.Tree(w.rects, w.ids, F)
+    rng = np.random.default_rng(100 + F)
+    sample = np.sort(rng.choice(w.queries.shape[0], 1500, replace=False))
+    for layout in ("soa", "aos"):
+        with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(),
+                      fanout=F, layout=layout) as t:
+            total = check_sample(rt, t, t_orc, w.queries, sample, F)
+        assert total > 10**8
+
+
+def test_uneven_10m_with_heavy_queries(rt):
+    import torch
+    w = dg.workload("uneven")
+    sizes = (w.queries[:, 2] - w.queries[:, 0]) * (w.queries[:, 3] - w.queries[:, 1])
+    heavy = np.nonzero(sizes > 0.05 * 0.05)[0]
+    rng = np.random.default_rng(7)
+    sample = np.sort(np.concatenate([rng.choice(heavy, min(150, heavy.size), replace=False),
+                                     rng.choice(w.queries.shape[0], 600, replace=False)]))
+    sample = np.unique(sample)
+    t_orc = oracle.Tree(w.rects, w.ids, 16)
+    with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(), fanout=16) as t:
+        check_sample(rt, t, t_orc, w.queries, sample, 16)
+
+
+def test_join_2m_x_2m_full(rt):
+    w = dg.workload("join")
+    want = oracle.Tree(w.rects, w.ids, 32).join(oracle.Tree(w.rects_s, w.ids_s, 32))
+    import torch
+    with rt.RTree(torch.from_numpy(w.rects).cuda(), None, fanout=32) as a, \
+            rt.RTree(torch.from_numpy(w.rects_s).cuda(), None, fanout=32) as b:
+        res = a.join(b)
+        _, got = res.to_numpy()
+        res.close()
+    assert np.array_equal(got, want) and len(want) > 10**5
