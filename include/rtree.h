@@ -169,6 +169,36 @@ RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *quer
                                 rtree_result_t **out);
 
 /*
+ * rtree_range_select_noalloc -- range select that allocates no device memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * For callers that cannot allocate once running: an application that has
+ * reserved all of the GPU's memory for its own pool, or a request loop that
+ * must neither block in nor fail from the CUDA allocator mid-request.  The
+ * caller passes every buffer; the library's temporary storage lives in one
+ * fixed device array (about 256 KiB) compiled into the library, which each
+ * GPU that loads the library holds until the process exits.
+ *
+ * queries: q*4 floats in device memory, 16-byte aligned, q <= 65536
+ *          (larger q: RTREE_EOVERFLOW; split the batch).
+ * offsets: device int64[q+1], receives the CSR offsets.
+ * ids:     device int32[capacity], receives the ids of query i at
+ *          ids[offsets[i] .. offsets[i+1]) in traversal order (not sorted;
+ *          the same order rtree_range_select gives with opts->unsorted = 1).
+ * total:   host int64, receives the number of ids.  If it exceeds capacity
+ *          the call returns RTREE_EOVERFLOW with offsets and *total valid
+ *          and ids unwritten, so the caller can retry with a larger buffer.
+ * The first call on a device looks up the array's device address (a
+ * runtime call, no allocation); make that first call before any stream
+ * capture.  Calls share the array: calls whose device work overlaps (other
+ * streams or host threads) race on it and must be serialized by the caller.
+ * Returns when the results are ready on `stream`.
+ */
+RTREE_API rtree_status rtree_range_select_noalloc(const rtree_t *tree, const float *queries, int64_t q,
+                                                  int64_t *offsets, int32_t *ids, int64_t capacity,
+                                                  int64_t *total, void *stream);
+
+/*
  * rtree_range_select_stats -- traversal counters of one count pass over the
  * same queries (no output is produced).  stats[0..5] receive: queries, nodes
  * visited, leaf nodes visited, children taken whole because their MBR lies

@@ -223,6 +223,13 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,
                           int mapping, cudaStream_t s, rtree_result *res);
 
+// One pass of the range-select kernel on caller-provided buffers: the count
+// pass when counts is non-null, else the scatter pass.  ctr (one zeroed
+// work counter) and flags (zeroed) are caller-provided; nothing is allocated.
+rtree_status select_pass(const rtree *t, const float4 *queries, int64_t q, int32_t *counts,
+                         const int64_t *offsets, int32_t *out, unsigned long long *ctr,
+                         int32_t *flags, cudaStream_t s);
+
 // Traversal statistics of one count pass (see rtree_range_select_stats).
 rtree_status select_stats(const rtree *t, const float4 *queries, int64_t q, cudaStream_t s,
                           int64_t out[8]);

@@ -295,6 +295,16 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     return RTREE_OK;
 }
 
+rtree_status select_pass(const rtree *t, const float4 *queries, int64_t Q, int32_t *counts,
+                         const int64_t *offsets, int32_t *out, unsigned long long *ctr,
+                         int32_t *flags, cudaStream_t s)
+{
+    SelectKernel k = pick(t->fanout, t->layout, counts ? PASS_COUNT : PASS_SCATTER);
+    if (!k)
+        return fail(RTREE_EINVAL, "unsupported fanout %d", t->fanout);
+    return launch(k, t, queries, Q, counts, offsets, out, ctr, flags, s);
+}
+
 rtree_status select_stats(const rtree *t, const float4 *queries, int64_t Q, cudaStream_t s,
                           int64_t out[8])
 {

@@ -64,6 +64,7 @@ def _bind(lib):
         "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
         "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
         "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
+        "rtree_range_select_noalloc": (C.c_int, [vp, vp, i64, vp, vp, i64, C.POINTER(C.c_int64), vp]),
         "rtree_result_total": (i64, [vp]),
         "rtree_result_rows": (i64, [vp]),
         "rtree_result_offsets": (vp, [vp]),
@@ -216,6 +217,23 @@ def rtree_range_select(handle: int, queries, unsorted: bool = False, mapping: st
     _check(lib.rtree_range_select(handle, qp, q, C.byref(opts), _stream(stream), C.byref(out)), lib)
     del keep
     return out.value
+
+
+def rtree_range_select_noalloc(handle: int, queries, offsets, ids, stream=None) -> int:
+    """Range select into caller-owned device tensors without any device
+    allocation (for callers that cannot allocate while running; see the C
+    header).  ``queries`` float32 [q, 4] (q <= 65536), ``offsets`` int64
+    [q+1], ``ids`` int32 [capacity], all CUDA tensors.  Returns the total;
+    raises RTreeError (RTREE_EOVERFLOW) when ids is too small, after
+    offsets have been written.  Ids come in traversal order."""
+    lib = load_library()
+    qp, q, keep = _as_rows(queries, "queries")
+    total = C.c_int64()
+    rc = lib.rtree_range_select_noalloc(handle, qp, q, offsets.data_ptr(), ids.data_ptr(),
+                                        ids.numel(), C.byref(total), _stream(stream))
+    del keep
+    _check(rc, lib)
+    return total.value
 
 
 def rtree_range_select_stats(handle: int, queries, stream=None) -> dict:
