@@ -165,3 +165,40 @@ def test_duplicate_and_extreme_ids(rt):
     want = oracle.Tree(rects, ids, 8).select(q)
     got = select_gpu(rt, rects, ids, q, fanout=8)
     assert_csr_equal(got, want, "duplicate ids")
+
+
+def test_long_segments_msd_and_skewed_fallback(rt):
+    """Segments longer than 16384 ids take the MSD partition; ids crowded
+    into one bucket take the global fallback.  Both must match the oracle."""
+    n = 120_000
+    rects = random_case("uniform", n, 77)
+    rng = np.random.default_rng(5)
+    spread = rng.permutation(n).astype(np.int32) * np.int32(7) - np.int32(400_000)
+    crowded = np.arange(n, dtype=np.int32)
+    crowded[::9999] += np.int32(1 << 30)      # a few far ids: most land in one bucket
+    queries = np.array([[-INF, -INF, INF, INF], [0.0, 0.0, 0.6, 0.7], [0.2, 0.1, 0.9, 0.5],
+                        [0.5, 0.5, 0.55, 0.55]], np.float32)
+    for ids in (spread, crowded):
+        want = oracle.Tree(rects, ids, 16).select(queries)
+        assert np.diff(want[0]).max() > 16384
+        for F in (16, 64):
+            got = select_gpu(rt, rects, ids, queries, fanout=F)
+            assert_csr_equal(got, want, f"long segments F={F}")
+
+
+def test_crowded_buckets_fall_back_to_lsd(rt):
+    """Dense id runs plus a few far outliers crowd the shared-memory buckets
+    of mid-size segments; the LSD fallback must give the same result."""
+    n = 40_000
+    rects = random_case("uniform", n, 91)
+    ids = np.arange(n, dtype=np.int32)
+    ids[::4000] += np.int32(1 << 22)
+    rng = np.random.default_rng(8)
+    lo = rng.random((60, 2)).astype(np.float32) * np.float32(0.7)
+    side = (rng.random((60, 1)) * 0.3).astype(np.float32)
+    queries = np.concatenate([lo, lo + side], axis=1).astype(np.float32)
+    want = oracle.Tree(rects, ids, 16).select(queries)
+    counts = np.diff(want[0])
+    assert ((counts > 256) & (counts <= 16384)).sum() > 20
+    got = select_gpu(rt, rects, ids, queries, fanout=16)
+    assert_csr_equal(got, want, "crowded buckets")
