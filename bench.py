@@ -49,6 +49,9 @@ def parse_args():
     ap.add_argument("--layout", choices=["soa", "aos", "auto"], default="auto")
     ap.add_argument("--n", type=int, default=None, help="override rectangles (testing only)")
     ap.add_argument("--q", type=int, default=None, help="override queries (testing only)")
+    ap.add_argument("--sel", type=float, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="override the query selectivity range (profiling a smaller index "
+                         "with the full-size hit-count mix)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-join", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -210,6 +213,9 @@ def run_ours(args):
 
     seed = 1 + 1000 * rank
     w = dg.workload(WORKLOAD, seed=seed, n=args.n, q=args.q)
+    if args.sel:
+        w.queries = dg.selectivity_queries(w.queries.shape[0], dg.rng_for(seed + 7), args.sel[0],
+                                           args.sel[1], dg._log_uniform_mean(1e-5, 1e-3))
     N, Q = w.rects.shape[0], w.queries.shape[0]
     rects = torch.from_numpy(w.rects).to(dev)
     ids = torch.from_numpy(w.ids).to(dev)

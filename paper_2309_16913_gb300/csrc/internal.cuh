@@ -211,7 +211,36 @@ rtree_status scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStre
 rtree_status radix_sort_pairs(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
                               uint32_t *vout, int64_t n, int bit_lo, int bit_hi, cudaStream_t s);
 
-// Sorts every segment ids[offsets[i] .. offsets[i+1]) ascending (signed).
+// Outputs of one select pass kernel (unused fields are null).
+struct SelIO {
+    int32_t *counts;          // COUNT: ids per query
+    int32_t *counts_leaf;     // COUNT, optional: ids found one by one in leaves
+    int32_t *counts_rng;      // COUNT, optional: whole subtrees taken
+    const int64_t *offsets;   // SCATTER: CSR offsets of the ids
+    int32_t *out;             // SCATTER: the ids, traversal order
+    const int64_t *off_leaf;  // DESC: offsets of the leaf hits
+    const int64_t *off_rng;   // DESC: offsets of the whole-subtree ranges
+    int32_t *leaf_out;        // DESC: leaf hits
+    int2 *rng_out;            // DESC: (lo, hi) ranges of the tree's id array
+};
+
+// Where the ids of segment i come from: leaf[off_leaf[i] .. off_leaf[i+1])
+// followed by tree_ids[lo .. hi) for every (lo, hi) in
+// rng[off_rng[i] .. off_rng[i+1]).  rng may be null (no ranges).
+struct SortSources {
+    const int32_t *leaf;
+    const int64_t *off_leaf;
+    const int2 *rng;
+    const int64_t *off_rng;
+    const int32_t *tree_ids;
+};
+
+// Writes segment i's ids, sorted ascending (signed), to
+// out[off[i] .. off[i+1]).  out may be the leaf array itself (in place).
+rtree_status segmented_sort_gather(int32_t *out, const int64_t *off, int64_t nseg, int64_t total,
+                                   const SortSources &src, cudaStream_t s);
+
+// Sorts every segment ids[offsets[i] .. offsets[i+1]) ascending, in place.
 rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
                             cudaStream_t s);
 

@@ -1,23 +1,25 @@
-// segsort.cu -- sort every query's id list ascending.
+// segsort.cu -- build every query's id list, sorted ascending.
 //
-// Results are sets; the traversal emits them in tree order, so each CSR
-// segment is sorted afterwards.  The work unit is sized to the segment:
-//   2..256 ids    one warp; bitonic network on 1-8 keys per lane held in
-//                 registers (shuffles across lanes, swaps inside a lane);
-//   257..16384    one CTA of 128-1024 threads, in shared memory with one
-//                 read and one write of DRAM: bucket the keys by their top
-//                 differing bits (2-4 keys per bucket for spread-out ids),
+// The select's traversal emits a query's ids in tree order, partly as single
+// leaf hits and partly as whole subtrees (contiguous runs of the tree's id
+// array).  This file gathers each query's ids from those sources and sorts
+// them, with the work unit sized to the segment:
+//   2..256 ids    one warp: gather into shared memory, then a bitonic network
+//                 on 1-8 keys per lane in registers (shuffles across lanes,
+//                 swaps inside a lane);
+//   257..16384    one CTA of 128-1024 threads, entirely in shared memory:
+//                 bucket the keys by their top differing bits (2-4 keys per
+//                 bucket for spread-out ids) with shared atomics and
 //                 insertion-sort each bucket; a crowded bucket sends the
-//                 segment to an LSD radix sort with 8-bit digits instead;
-//   > 16384       one CTA partitions the segment by its top differing bits
-//                 into buckets of about 8K ids (MSD step, through a scratch
-//                 area), then every bucket is sorted by the CTA radix sort
-//                 and written back in place.
-// LSD passes whose digit is equal for all keys are skipped (from the AND
-// and OR of the keys).  In each LSD pass a key's rank among equal digits
-// comes from walking the keys in order: each warp owns a contiguous run and
-// takes it 32 at a time, with __match_any_sync grouping equal digits.  Keys
-// are ids with the sign bit flipped, so unsigned order is signed order.
+//                 segment to a stable LSD radix sort (8-bit digits);
+//   > 16384       gathered into place, partitioned by its top differing bits
+//                 into buckets of about 8K ids (MSD step through a scratch
+//                 area), each bucket then sorted like a mid-size segment.
+// LSD passes whose digit is equal for all keys are skipped (from the AND and
+// OR of the keys).  In each LSD pass a key's rank among equal digits comes
+// from walking the keys in order: each warp owns a contiguous run and takes it
+// 32 at a time, with __match_any_sync grouping equal digits.  Keys are ids
+// with the sign bit flipped, so unsigned order is signed order.
 #include <climits>
 
 #include "internal.cuh"
@@ -26,15 +28,17 @@ namespace rt {
 namespace {
 
 constexpr int kBins = 256;
-constexpr int kItems = 16;                 // keys per thread in the CTA sort
-constexpr int kCtaMax = 1024 * kItems;     // 16384: largest in-shared-memory segment
+constexpr int kItems = 16;              // keys per thread in the CTA sort
+constexpr int kCtaMax = 1024 * kItems;  // 16384: largest in-shared-memory segment
 constexpr uint32_t kSign = 0x80000000u;
+constexpr int kBucketBitsMax = 12;      // at most 4096 buckets
+constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to LSD
 
 // Segment classes (index into the class lists).
 enum {
-    C_W1 = 0, C_W2, C_W4, C_W8,          // warp sorts, 32*K ids
-    C_T128, C_T256, C_T512, C_T1024,     // CTA sorts, 16 ids per thread
-    C_LARGE,                             // MSD partition first
+    C_W1 = 0, C_W2, C_W4, C_W8,       // warp sorts, 32*K ids
+    C_T128, C_T256, C_T512, C_T1024,  // CTA sorts, 16 ids per thread
+    C_LARGE,                          // MSD partition first
     C_COUNT
 };
 enum { HDR_SCRATCH = C_COUNT, HDR_BUCKETS, HDR_OVERSIZE, HDR_WORDS };
@@ -60,9 +64,11 @@ __device__ __forceinline__ int class_of(int64_t n)
     return C_LARGE;
 }
 
+// Segments of length 1 are written directly (class -1 otherwise).
 __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_t *__restrict__ lists,
                            int64_t stride, int64_t *__restrict__ large_tmp,
-                           unsigned long long *__restrict__ hdr)
+                           unsigned long long *__restrict__ hdr, SortSources S,
+                           int32_t *__restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -72,6 +78,14 @@ __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_
         const int64_t i = b + lane;
         const int64_t len = i < nseg ? off[i + 1] - off[i] : 0;
         const int cls = class_of(len);
+        if (len == 1) {  // a single id: copy it from its source
+            int32_t v;
+            if (S.off_leaf[i + 1] > S.off_leaf[i])
+                v = S.leaf[S.off_leaf[i]];
+            else
+                v = S.tree_ids[S.rng[S.off_rng[i]].x];
+            out[off[i]] = v;
+        }
         for (int c = 0; c < C_COUNT; ++c) {
             const unsigned m = __ballot_sync(RT_FULL, cls == c);
             if (!m)
@@ -91,27 +105,72 @@ __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_
     }
 }
 
+// ------------------------------------------------------------- gathering
+// One warp copies segment i's ids into sm[0 .. n) (in source order).
+__device__ __forceinline__ void warp_gather(int32_t *__restrict__ sm, const SortSources &S,
+                                            int64_t i, int lane)
+{
+    const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+    for (int64_t e = l0 + lane; e < l1; e += 32)
+        sm[e - l0] = S.leaf[e];
+    int pos = (int)(l1 - l0);
+    if (S.rng) {
+        const int64_t r0 = S.off_rng[i], r1 = S.off_rng[i + 1];
+        for (int64_t rb = r0; rb < r1; rb += 32) {
+            // lanes hold up to 32 ranges; an inclusive scan of their lengths
+            // gives each range's place, then the warp copies them in turn
+            const int64_t r = rb + lane;
+            int2 rg = make_int2(0, 0);
+            if (r < r1)
+                rg = S.rng[r];
+            const int len = rg.y - rg.x;
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(RT_FULL, inc, o);
+                if (lane >= o)
+                    inc += u;
+            }
+            const int start = pos + inc - len;
+            const int cnt = (int)(r1 - rb < 32 ? r1 - rb : 32);
+            for (int k = 0; k < cnt; ++k) {
+                const int lo = __shfl_sync(RT_FULL, rg.x, k);
+                const int ln = __shfl_sync(RT_FULL, len, k);
+                const int st = __shfl_sync(RT_FULL, start, k);
+                for (int e = lane; e < ln; e += 32)
+                    sm[st + e] = __ldg(S.tree_ids + lo + e);
+            }
+            pos += __shfl_sync(RT_FULL, inc, 31);
+        }
+    }
+    __syncwarp();
+}
+
 // ----------------------------------------------------------- warp sorts
 // Bitonic sort of up to 32*K signed ids; element e = k*32 + lane (striped).
 template <int K>
 __global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ list, int64_t cnt,
-                                                   const int64_t *__restrict__ off,
-                                                   int32_t *__restrict__ ids)
+                                                   const int64_t *__restrict__ off, SortSources S,
+                                                   int32_t *__restrict__ out)
 {
     constexpr int N = 32 * K;
+    __shared__ int32_t stage[8][N];
     const int lane = threadIdx.x & 31;
+    int32_t *sm = stage[threadIdx.x >> 5];
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t wi = warp; wi < cnt; wi += nwarps) {
         const int32_t seg = list[wi];
         const int64_t o = off[seg];
         const int n = (int)(off[seg + 1] - o);
+        warp_gather(sm, S, seg, lane);
         int v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int e = k * 32 + lane;
-            v[k] = e < n ? ids[o + e] : INT_MAX;
+            v[k] = e < n ? sm[e] : INT_MAX;
         }
+        __syncwarp();
 #pragma unroll
         for (int size = 2; size <= N; size <<= 1) {
 #pragma unroll
@@ -144,25 +203,27 @@ __global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ l
         for (int k = 0; k < K; ++k) {
             const int e = k * 32 + lane;
             if (e < n)
-                ids[o + e] = v[k];
+                out[o + e] = v[k];
         }
     }
 }
 
 // ------------------------------------------------------------ CTA sort
-constexpr int kBucketBitsMax = 12;  // at most 4096 buckets
-constexpr int kBucketCrowded = 32;  // a bucket longer than this sends the segment to LSD
-
 template <int THREADS>
 struct CtaSmem {
     static constexpr int W = THREADS / 32;
     uint32_t buf[THREADS * kItems];
     union {
         uint32_t cnt[1 << kBucketBitsMax];  // bucket sort: per-bucket counts, then ends
-        struct {
+        struct {                            // LSD ranks
             uint32_t wcnt[W][kBins];
             uint32_t dcount[kBins];
             uint32_t dstart[kBins];
+        };
+        struct {                            // gathering: one chunk of ranges
+            int32_t rlo[THREADS];
+            int32_t rstart[THREADS];
+            int32_t rlen[THREADS];
         };
     };
     uint32_t wsum[W];
@@ -170,9 +231,259 @@ struct CtaSmem {
     uint32_t crowded;
 };
 
+// Exclusive block scan of one int per thread (uses sm.wsum); returns the
+// prefix and writes the block total to *total.
+template <int THREADS>
+__device__ __forceinline__ int block_scan_int(CtaSmem<THREADS> &sm, int v, int *total)
+{
+    constexpr int W = THREADS / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(RT_FULL, inc, o);
+        if (lane >= o)
+            inc += u;
+    }
+    if (lane == 31)
+        sm.wsum[w] = (uint32_t)inc;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int x = 0; x < W; ++x) {
+        const int s = (int)sm.wsum[x];
+        if (x < w)
+            before += s;
+        all += s;
+    }
+    *total = all;
+    __syncthreads();
+    return before + inc - v;
+}
+
+// The CTA copies segment i's ids into sm.buf[0 .. n), flipped to keys.
+template <int THREADS>
+__device__ __forceinline__ void cta_gather(CtaSmem<THREADS> &sm, const SortSources &S, int64_t i)
+{
+    constexpr int W = THREADS / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+    for (int64_t e = l0 + threadIdx.x; e < l1; e += THREADS)
+        sm.buf[e - l0] = (uint32_t)S.leaf[e] ^ kSign;
+    int pos = (int)(l1 - l0);
+    if (S.rng) {
+        const int64_t r0 = S.off_rng[i], r1 = S.off_rng[i + 1];
+        for (int64_t rb = r0; rb < r1; rb += THREADS) {
+            const int64_t r = rb + threadIdx.x;
+            int2 rg = make_int2(0, 0);
+            if (r < r1)
+                rg = S.rng[r];
+            const int len = rg.y - rg.x;
+            int total;
+            const int start = block_scan_int<THREADS>(sm, len, &total);
+            sm.rlo[threadIdx.x] = rg.x;
+            sm.rlen[threadIdx.x] = len;
+            sm.rstart[threadIdx.x] = pos + start;
+            __syncthreads();
+            const int cnt = (int)(r1 - rb < THREADS ? r1 - rb : THREADS);
+            for (int k = w; k < cnt; k += W) {  // warp w copies ranges w, w+W, ...
+                const int lo = sm.rlo[k], ln = sm.rlen[k], st = sm.rstart[k];
+                for (int e = lane; e < ln; e += 32)
+                    sm.buf[st + e] = (uint32_t)__ldg(S.tree_ids + lo + e) ^ kSign;
+            }
+            pos += total;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+}
+
+// The CTA copies keys src[0 .. n) (xor flip) into sm.buf.
+template <int THREADS>
+__device__ __forceinline__ void cta_load(CtaSmem<THREADS> &sm, const uint32_t *__restrict__ src,
+                                         int n, uint32_t flip)
+{
+    for (int p = threadIdx.x; p < n; p += THREADS)
+        sm.buf[p] = src[p] ^ flip;
+    __syncthreads();
+}
+
+// Block-wide AND and OR of the keys' bits; every thread gets AND ^ OR.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_and, uint32_t a_or)
+{
+    constexpr int W = THREADS / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        a_and &= __shfl_xor_sync(RT_FULL, a_and, d);
+        a_or |= __shfl_xor_sync(RT_FULL, a_or, d);
+    }
+    if (lane == 0) {
+        sm.red_and[w] = a_and;
+        sm.red_or[w] = a_or;
+    }
+    __syncthreads();
+    a_and = 0xffffffffu;
+    a_or = 0;
+    for (int x = 0; x < W; ++x) {
+        a_and &= sm.red_and[x];
+        a_or |= sm.red_or[x];
+    }
+    __syncthreads();
+    return a_and ^ a_or;
+}
+
+// Sorts the n <= THREADS*kItems keys in sm.buf and writes them to dst (xor
+// kSign back to ids).  Keys are bucketed by their top B differing bits (B
+// about log2(n) - 1, at most 12) with shared atomics, then each bucket is
+// insertion-sorted; the order inside a bucket before that does not matter.
+// Returns false, having written the unsorted ids to dst, if a bucket holds
+// more than kBucketCrowded keys (the caller then sorts dst with LSD).
+template <int THREADS>
+__device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *__restrict__ dst,
+                                                int n)
+{
+    uint32_t key[kItems];
+    uint32_t a_and = 0xffffffffu, a_or = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (i * THREADS >= n)
+            break;
+        const int p = i * THREADS + threadIdx.x;
+        key[i] = 0;
+        if (p < n) {
+            key[i] = sm.buf[p];
+            a_and &= key[i];
+            a_or |= key[i];
+        }
+    }
+    const uint32_t diff = block_diff<THREADS>(sm, a_and, a_or);
+    if (diff == 0) {  // all keys equal
+        for (int p = threadIdx.x; p < n; p += THREADS)
+            dst[p] = (int32_t)(sm.buf[p] ^ kSign);
+        __syncthreads();
+        return true;
+    }
+    const int hb = 31 - __clz(diff);
+    int bits = (32 - __clz((unsigned)(n - 1))) - 1;  // ceil(log2 n) - 1
+    bits = bits < 1 ? 1 : (bits > kBucketBitsMax ? kBucketBitsMax : bits);
+    if (bits > hb + 1)
+        bits = hb + 1;
+    const int shift = hb + 1 - bits;
+    const int nb = 1 << bits;
+    const uint32_t mask = (uint32_t)nb - 1u;
+    for (int b = threadIdx.x; b < nb; b += THREADS)
+        sm.cnt[b] = 0;
+    if (threadIdx.x == 0)
+        sm.crowded = 0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (i * THREADS >= n)
+            break;
+        if (i * THREADS + threadIdx.x < n)
+            atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    {  // exclusive scan of the nb counts: each thread owns a run of them
+        const int per = (nb + THREADS - 1) / THREADS;
+        const int lo = threadIdx.x * per;
+        int sum = 0;
+        for (int b = lo; b < lo + per && b < nb; ++b)
+            sum += (int)sm.cnt[b];
+        int total;
+        int run = block_scan_int<THREADS>(sm, sum, &total);
+        for (int b = lo; b < lo + per && b < nb; ++b) {
+            const int c = (int)sm.cnt[b];
+            if (c > kBucketCrowded)
+                sm.crowded = 1;
+            sm.cnt[b] = (uint32_t)run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (sm.crowded) {
+        for (int p = threadIdx.x; p < n; p += THREADS)
+            dst[p] = (int32_t)(sm.buf[p] ^ kSign);
+        __syncthreads();
+        return false;
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (i * THREADS >= n)
+            break;
+        if (i * THREADS + threadIdx.x < n) {
+            const uint32_t pos = atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
+            sm.buf[pos] = key[i];
+        }
+    }
+    __syncthreads();
+    // cnt[b] is now the end of bucket b; sort each bucket by insertion
+    for (int b = threadIdx.x; b < nb; b += THREADS) {
+        const int e = (int)sm.cnt[b];
+        const int s0 = b ? (int)sm.cnt[b - 1] : 0;
+        for (int i = s0 + 1; i < e; ++i) {
+            const uint32_t x = sm.buf[i];
+            int j = i - 1;
+            while (j >= s0 && sm.buf[j] > x) {
+                sm.buf[j + 1] = sm.buf[j];
+                --j;
+            }
+            sm.buf[j + 1] = x;
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += THREADS)
+        dst[p] = (int32_t)(sm.buf[p] ^ kSign);
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void push_crowded(SegDesc *list, unsigned long long *count, int64_t cap,
+                                             int64_t dst, int n)
+{
+    const unsigned long long slot = atomicAdd(count, 1ull);
+    if ((int64_t)slot < cap)
+        list[slot] = SegDesc{dst, dst, n, 0};
+}
+
+// One CTA per listed segment.  BUCKETS: the list holds SegDesc entries whose
+// keys sit in `scratch`; otherwise segment ids whose ids are gathered from S.
+template <int THREADS, bool BUCKETS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+    k_sort_cta(const void *__restrict__ list, int64_t cnt, const int64_t *__restrict__ off,
+               SortSources S, const uint32_t *__restrict__ scratch, int32_t *__restrict__ out,
+               SegDesc *__restrict__ crowded, unsigned long long *__restrict__ n_crowded,
+               int64_t crowded_cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CtaSmem<THREADS> &sm = *reinterpret_cast<CtaSmem<THREADS> *>(smem_raw);
+    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
+        int64_t dof;
+        int n;
+        if (BUCKETS) {
+            const SegDesc d = static_cast<const SegDesc *>(list)[b];
+            dof = d.dst;
+            n = d.n;
+            if (n > THREADS * kItems)
+                continue;
+            cta_load<THREADS>(sm, scratch + d.src, n, 0u);
+        } else {
+            const int32_t seg = static_cast<const int32_t *>(list)[b];
+            dof = off[seg];
+            n = (int)(off[seg + 1] - dof);
+            if (n > THREADS * kItems)
+                continue;
+            cta_gather<THREADS>(sm, S, seg);
+        }
+        if (!cta_bucket_sort<THREADS>(sm, out + dof, n) && threadIdx.x == 0)
+            push_crowded(crowded, n_crowded, crowded_cap, dof, n);
+    }
+}
+
 // Ranks the keys held in registers for one LSD pass; on return pos[i] is the
-// position of key[i] in the pass's output order (valid where i < rounds and
-// the key exists).  Warp w owns keys [w*run, (w+1)*run), taken 32 at a time.
+// position of key[i] in the pass's output order.  Warp w owns keys
+// [w*run, (w+1)*run), taken 32 at a time.
 template <int THREADS>
 __device__ __forceinline__ void rank_pass(CtaSmem<THREADS> &sm, const uint32_t (&key)[kItems],
                                           int rounds, int run, int n, int shift,
@@ -186,17 +497,17 @@ __device__ __forceinline__ void rank_pass(CtaSmem<THREADS> &sm, const uint32_t (
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        if (i < rounds) {
-            const bool ok = w * run + i * 32 + lane < n;
-            const int dg = ok ? (int)((key[i] >> shift) & 0xffu) : kBins;
-            const unsigned peers = __match_any_sync(RT_FULL, dg);
-            const uint32_t prev = ok ? sm.wcnt[w][dg] : 0u;
-            pos[i] = prev + __popc(peers & lt);
-            __syncwarp();
-            if (ok && lane == __ffs(peers) - 1)
-                sm.wcnt[w][dg] = prev + __popc(peers);
-            __syncwarp();
-        }
+        if (i >= rounds)
+            break;
+        const bool ok = w * run + i * 32 + lane < n;
+        const int dg = ok ? (int)((key[i] >> shift) & 0xffu) : kBins;
+        const unsigned peers = __match_any_sync(RT_FULL, dg);
+        const uint32_t prev = ok ? sm.wcnt[w][dg] : 0u;
+        pos[i] = prev + __popc(peers & lt);
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1)
+            sm.wcnt[w][dg] = prev + __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kBins; d += THREADS) {
@@ -229,21 +540,19 @@ __device__ __forceinline__ void rank_pass(CtaSmem<THREADS> &sm, const uint32_t (
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        if (i < rounds && w * run + i * 32 + lane < n) {
+        if (i >= rounds)
+            break;
+        if (w * run + i * 32 + lane < n) {
             const int dg = (int)((key[i] >> shift) & 0xffu);
             pos[i] += sm.dstart[dg] + sm.wcnt[w][dg];
         }
     }
 }
 
-// Sorts one segment of n <= THREADS*kItems keys: src keys (xor flip_in)
-// -> dst ids (xor flip_out).
-template <int THREADS>
-__device__ __forceinline__ void cta_sort_one(CtaSmem<THREADS> &sm, const uint32_t *__restrict__ src,
-                                             uint32_t *__restrict__ dst, int n, uint32_t flip_in,
-                                             uint32_t flip_out)
+// Stable LSD radix sort of n <= 16384 ids in place at ids[0 .. n).
+__device__ __forceinline__ void cta_lsd_sort(CtaSmem<1024> &sm, int32_t *__restrict__ ids, int n)
 {
-    constexpr int W = THREADS / 32;
+    constexpr int THREADS = 1024, W = 32;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int run = ((n + W * 32 - 1) / (W * 32)) * 32;
     const int rounds = run / 32;
@@ -254,42 +563,16 @@ __device__ __forceinline__ void cta_sort_one(CtaSmem<THREADS> &sm, const uint32_
         key[i] = 0;
         const int p = w * run + i * 32 + lane;
         if (i < rounds && p < n) {
-            key[i] = src[p] ^ flip_in;
+            key[i] = (uint32_t)ids[p] ^ kSign;
             a_and &= key[i];
             a_or |= key[i];
         }
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        a_and &= __shfl_xor_sync(RT_FULL, a_and, d);
-        a_or |= __shfl_xor_sync(RT_FULL, a_or, d);
-    }
-    if (lane == 0) {
-        sm.red_and[w] = a_and;
-        sm.red_or[w] = a_or;
-    }
-    __syncthreads();
-    a_and = 0xffffffffu;
-    a_or = 0;
-    for (int x = 0; x < W; ++x) {
-        a_and &= sm.red_and[x];
-        a_or |= sm.red_or[x];
-    }
-    const uint32_t diff = a_and ^ a_or;
+    const uint32_t diff = block_diff<THREADS>(sm, a_and, a_or);
     int last = -1;
     for (int shift = 0; shift < 32; shift += 8)
         if ((diff >> shift) & 0xffu)
             last = shift;
-    if (last < 0) {  // all keys equal: already sorted
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const int p = w * run + i * 32 + lane;
-            if (i < rounds && p < n)
-                dst[p] = key[i] ^ flip_out;
-        }
-        __syncthreads();
-        return;
-    }
     for (int shift = 0; shift <= last; shift += 8) {
         if (((diff >> shift) & 0xffu) == 0)
             continue;
@@ -301,7 +584,7 @@ __device__ __forceinline__ void cta_sort_one(CtaSmem<THREADS> &sm, const uint32_
         __syncthreads();
         if (shift == last) {
             for (int p = threadIdx.x; p < n; p += THREADS)
-                dst[p] = sm.buf[p] ^ flip_out;
+                ids[p] = (int32_t)(sm.buf[p] ^ kSign);
         } else {
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
@@ -314,201 +597,11 @@ __device__ __forceinline__ void cta_sort_one(CtaSmem<THREADS> &sm, const uint32_
     }
 }
 
-// Block-wide AND and OR of the keys' bits; every thread gets the result.
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_and, uint32_t a_or)
-{
-    constexpr int W = THREADS / 32;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        a_and &= __shfl_xor_sync(RT_FULL, a_and, d);
-        a_or |= __shfl_xor_sync(RT_FULL, a_or, d);
-    }
-    if (lane == 0) {
-        sm.red_and[w] = a_and;
-        sm.red_or[w] = a_or;
-    }
-    __syncthreads();
-    a_and = 0xffffffffu;
-    a_or = 0;
-    for (int x = 0; x < W; ++x) {
-        a_and &= sm.red_and[x];
-        a_or |= sm.red_or[x];
-    }
-    __syncthreads();
-    return a_and ^ a_or;
-}
-
-// Sorts one segment of n <= THREADS*kItems keys by bucketing on the top B
-// bits that differ between its keys (B about log2(n) - 1, at most 12, so a
-// bucket holds 2-4 keys on average for spread-out ids), then sorting each
-// bucket by insertion.  Buckets are filled with shared-memory atomics (the
-// order inside a bucket does not matter: the bucket is sorted next).  If any
-// bucket holds more than kBucketCrowded keys the segment is re-sorted by the
-// stable LSD radix path instead, so skewed id sets stay correct and cheap.
-// Returns false (writing nothing) if a bucket is crowded.
-template <int THREADS>
-__device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, const uint32_t *__restrict__ src,
-                                                uint32_t *__restrict__ dst, int n, uint32_t flip_in,
-                                                uint32_t flip_out)
-{
-    uint32_t key[kItems];
-    uint32_t a_and = 0xffffffffu, a_or = 0;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int p = i * THREADS + threadIdx.x;
-        if (i * THREADS >= n)
-            break;
-        key[i] = 0;
-        if (p < n) {
-            key[i] = src[p] ^ flip_in;
-            a_and &= key[i];
-            a_or |= key[i];
-        }
-    }
-    const uint32_t diff = block_diff<THREADS>(sm, a_and, a_or);
-    if (diff == 0) {  // all keys equal
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            const int p = i * THREADS + threadIdx.x;
-            if (i * THREADS >= n)
-                break;
-            if (p < n)
-                dst[p] = key[i] ^ flip_out;
-        }
-        __syncthreads();
-        return true;
-    }
-    const int hb = 31 - __clz(diff);
-    int bits = 32 - __clz((unsigned)(n - 1));  // ceil(log2(n)) for n >= 2
-    bits = bits - 1;
-    bits = bits < 1 ? 1 : (bits > kBucketBitsMax ? kBucketBitsMax : bits);
-    if (bits > hb + 1)
-        bits = hb + 1;
-    const int shift = hb + 1 - bits;
-    const int nb = 1 << bits;
-    const uint32_t mask = (uint32_t)nb - 1u;
-    for (int b = threadIdx.x; b < nb; b += THREADS)
-        sm.cnt[b] = 0;
-    if (threadIdx.x == 0)
-        sm.crowded = 0;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        if (i * THREADS >= n)
-            break;
-        if (i * THREADS + threadIdx.x < n)
-            atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    {  // exclusive scan of the nb counts: each thread owns a run of them
-        constexpr int W = THREADS / 32;
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        const int per = (nb + THREADS - 1) / THREADS;
-        const int lo = threadIdx.x * per;
-        uint32_t sum = 0;
-        for (int b = lo; b < lo + per && b < nb; ++b)
-            sum += sm.cnt[b];
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(RT_FULL, inc, o);
-            if (lane >= o)
-                inc += u;
-        }
-        if (lane == 31)
-            sm.wsum[w] = inc;
-        __syncthreads();
-        uint32_t run = inc - sum;
-        for (int x = 0; x < w; ++x)
-            run += sm.wsum[x];
-        for (int b = lo; b < lo + per && b < nb; ++b) {
-            const uint32_t c = sm.cnt[b];
-            if (c > (uint32_t)kBucketCrowded)
-                sm.crowded = 1;
-            sm.cnt[b] = run;
-            run += c;
-        }
-        (void)W;
-    }
-    __syncthreads();
-    if (sm.crowded) {
-        __syncthreads();
-        return false;
-    }
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        if (i * THREADS >= n)
-            break;
-        if (i * THREADS + threadIdx.x < n) {
-            const uint32_t pos = atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
-            sm.buf[pos] = key[i];
-        }
-    }
-    __syncthreads();
-    // cnt[b] is now the end of bucket b; sort each bucket by insertion
-    for (int b = threadIdx.x; b < nb; b += THREADS) {
-        const int e = (int)sm.cnt[b];
-        const int s0 = b ? (int)sm.cnt[b - 1] : 0;
-        for (int i = s0 + 1; i < e; ++i) {
-            const uint32_t x = sm.buf[i];
-            int j = i - 1;
-            while (j >= s0 && sm.buf[j] > x) {
-                sm.buf[j + 1] = sm.buf[j];
-                --j;
-            }
-            sm.buf[j + 1] = x;
-        }
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < n; p += THREADS)
-        dst[p] = sm.buf[p] ^ flip_out;
-    __syncthreads();
-    return true;
-}
-
-// One CTA per listed segment (BUCKETS: list of SegDesc; else segment ids).
-// Segments with a crowded bucket are appended to `crowded` for k_sort_lsd.
-template <int THREADS, bool BUCKETS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-    k_sort_cta(const void *__restrict__ list, int64_t cnt, const int64_t *__restrict__ off,
-               const uint32_t *__restrict__ src_base, uint32_t *__restrict__ dst_base,
-               uint32_t flip_in, uint32_t flip_out, SegDesc *__restrict__ crowded,
-               unsigned long long *__restrict__ n_crowded, int64_t crowded_cap)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaSmem<THREADS> &sm = *reinterpret_cast<CtaSmem<THREADS> *>(smem_raw);
-    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
-        int64_t so, dof;
-        int n;
-        if (BUCKETS) {
-            const SegDesc d = static_cast<const SegDesc *>(list)[b];
-            so = d.src;
-            dof = d.dst;
-            n = d.n;
-        } else {
-            const int32_t seg = static_cast<const int32_t *>(list)[b];
-            so = dof = off[seg];
-            n = (int)(off[seg + 1] - so);
-        }
-        if (n > THREADS * kItems)
-            continue;  // never listed here; guarded anyway
-        if (!cta_bucket_sort<THREADS>(sm, src_base + so, dst_base + dof, n, flip_in, flip_out) &&
-            threadIdx.x == 0) {
-            const unsigned long long slot = atomicAdd(n_crowded, 1ull);
-            if ((int64_t)slot < crowded_cap)
-                crowded[slot] = SegDesc{so, dof, n, 0};
-        }
-    }
-}
-
-// Stable LSD radix sort (in shared memory) of the segments whose buckets
-// were crowded.  Persistent: the list length is read on the device.
+// Segments whose buckets were crowded, sorted in place by LSD radix.
+// Persistent: the list length is read on the device.
 __global__ void __launch_bounds__(1024, 1)
     k_sort_lsd(const SegDesc *__restrict__ list, const unsigned long long *__restrict__ count,
-               int64_t cap, const uint32_t *__restrict__ src_base, uint32_t *__restrict__ dst_base,
-               uint32_t flip_in, uint32_t flip_out)
+               int64_t cap, int32_t *__restrict__ out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem<1024> &sm = *reinterpret_cast<CtaSmem<1024> *>(smem_raw);
@@ -519,11 +612,67 @@ __global__ void __launch_bounds__(1024, 1)
         const SegDesc d = list[b];
         if (d.n > 1024 * kItems)
             continue;
-        cta_sort_one<1024>(sm, src_base + d.src, dst_base + d.dst, d.n, flip_in, flip_out);
+        cta_lsd_sort(sm, out + d.dst, d.n);
     }
 }
 
 // ------------------------------------------------------------ MSD step
+// Gathers each long segment into its place in `out` (unsorted).
+__global__ void __launch_bounds__(1024)
+    k_gather_large(const int32_t *__restrict__ list, int64_t cnt, const int64_t *__restrict__ off,
+                   SortSources S, int32_t *__restrict__ out)
+{
+    __shared__ int32_t rstart[1024];
+    __shared__ int32_t wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
+        const int32_t i = list[b];
+        int32_t *dst = out + off[i];
+        const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+        if (S.leaf + l0 != dst)
+            for (int64_t e = l0 + threadIdx.x; e < l1; e += 1024)
+                dst[e - l0] = S.leaf[e];
+        int64_t pos = l1 - l0;
+        if (!S.rng)
+            continue;
+        const int64_t r0 = S.off_rng[i], r1 = S.off_rng[i + 1];
+        for (int64_t rb = r0; rb < r1; rb += 1024) {
+            const int64_t r = rb + threadIdx.x;
+            int2 rg = make_int2(0, 0);
+            if (r < r1)
+                rg = S.rng[r];
+            const int len = rg.y - rg.x;
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(RT_FULL, inc, o);
+                if (lane >= o)
+                    inc += u;
+            }
+            if (lane == 31)
+                wsum[w] = inc;
+            __syncthreads();
+            int before = 0, all = 0;
+            for (int x = 0; x < 32; ++x) {
+                if (x < w)
+                    before += wsum[x];
+                all += wsum[x];
+            }
+            rstart[threadIdx.x] = before + inc - len;
+            __syncthreads();
+            const int cntr = (int)(r1 - rb < 1024 ? r1 - rb : 1024);
+            for (int k = w; k < cntr; k += 32) {
+                const int2 g = S.rng[rb + k];
+                const int64_t st = pos + rstart[k];
+                for (int e = lane; e < g.y - g.x; e += 32)
+                    dst[st + e] = __ldg(S.tree_ids + g.x + e);
+            }
+            pos += all;
+            __syncthreads();
+        }
+    }
+}
+
 // One CTA per segment longer than kCtaMax: partitions its keys by their top
 // b differing bits (2^b buckets of about kCtaMax/2) into the scratch area and
 // lists every bucket for the CTA sort (or, if a bucket is still too long,
@@ -626,9 +775,9 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// Fallback for buckets longer than kCtaMax (heavily skewed ids): copy the
-// bucket to its destination, then LSD radix sort it there through global
-// memory, using the bucket's scratch range as the second buffer.
+// Fallback for buckets longer than kCtaMax (heavily skewed ids): LSD radix
+// sort through global memory from the bucket's scratch range (keys) to its
+// place in the output, ping-ponging between the two.
 __global__ void __launch_bounds__(256)
     k_sort_global(const SegDesc *__restrict__ list, int64_t cnt, uint32_t *__restrict__ scratch,
                   int32_t *__restrict__ ids)
@@ -638,8 +787,8 @@ __global__ void __launch_bounds__(256)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
         const SegDesc d = list[b];
-        uint32_t *x = scratch + d.src;                              // keys (flipped)
-        uint32_t *y = reinterpret_cast<uint32_t *>(ids) + d.dst;    // output area
+        uint32_t *x = scratch + d.src;                            // keys (flipped)
+        uint32_t *y = reinterpret_cast<uint32_t *>(ids) + d.dst;  // output area
         const int64_t n = d.n;
         uint32_t a_and = 0xffffffffu, a_or = 0;
         for (int64_t p = threadIdx.x; p < n; p += 256) {
@@ -717,6 +866,7 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// --------------------------------------------------------------- launches
 template <typename K>
 rtree_status set_smem(K kern, size_t bytes)
 {
@@ -732,9 +882,9 @@ struct Crowded {
 };
 
 template <int THREADS, bool BUCKETS>
-rtree_status launch_cta(const void *list, int64_t cnt, const int64_t *off, const uint32_t *src,
-                        uint32_t *dst, uint32_t flip_in, uint32_t flip_out, const Crowded &cr,
-                        cudaStream_t s, const char *name)
+rtree_status launch_cta(const void *list, int64_t cnt, const int64_t *off, const SortSources &S,
+                        const uint32_t *scratch, int32_t *out, const Crowded &cr, cudaStream_t s,
+                        const char *name)
 {
     if (cnt <= 0)
         return RTREE_OK;
@@ -747,27 +897,25 @@ rtree_status launch_cta(const void *list, int64_t cnt, const int64_t *off, const
     if (grid > cnt)
         grid = cnt;
     KernelTimer kt_(name, s);
-    kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, cnt, off, src, dst, flip_in, flip_out,
-                                                cr.list, cr.count, cr.cap);
+    kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, cnt, off, S, scratch, out, cr.list, cr.count,
+                                                cr.cap);
     RT_LAUNCH();
     return RTREE_OK;
 }
 
-rtree_status launch_lsd(const Crowded &cr, const uint32_t *src, uint32_t *dst, uint32_t flip_in,
-                        uint32_t flip_out, cudaStream_t s)
+rtree_status launch_lsd(const Crowded &cr, int32_t *out, cudaStream_t s)
 {
     const size_t bytes = sizeof(CtaSmem<1024>);
     RT_TRY(set_smem(k_sort_lsd, bytes));
     KernelTimer kt_("sort_lsd", s);
-    k_sort_lsd<<<(unsigned)sm_count(), 1024, bytes, s>>>(cr.list, cr.count, cr.cap, src, dst, flip_in,
-                                                         flip_out);
+    k_sort_lsd<<<(unsigned)sm_count(), 1024, bytes, s>>>(cr.list, cr.count, cr.cap, out);
     RT_LAUNCH();
     return RTREE_OK;
 }
 
 template <int K>
-rtree_status launch_warp(const int32_t *list, int64_t cnt, const int64_t *off, int32_t *ids,
-                         cudaStream_t s)
+rtree_status launch_warp(const int32_t *list, int64_t cnt, const int64_t *off, const SortSources &S,
+                         int32_t *out, cudaStream_t s)
 {
     if (cnt <= 0)
         return RTREE_OK;
@@ -776,17 +924,17 @@ rtree_status launch_warp(const int32_t *list, int64_t cnt, const int64_t *off, i
     if (blocks > cap)
         blocks = cap;
     KernelTimer kt_("sort_warp", s);
-    k_sort_warp<K><<<(unsigned)blocks, 256, 0, s>>>(list, cnt, off, ids);
+    k_sort_warp<K><<<(unsigned)blocks, 256, 0, s>>>(list, cnt, off, S, out);
     RT_LAUNCH();
     return RTREE_OK;
 }
 
 }  // namespace
 
-rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
-                            cudaStream_t s)
+rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t nseg, int64_t total,
+                                   const SortSources &S, cudaStream_t s)
 {
-    if (nseg <= 0 || total <= 1)
+    if (nseg <= 0 || total <= 0)
         return RTREE_OK;
     if (nseg >= (int64_t)INT32_MAX)
         return fail(RTREE_EOVERFLOW, "too many segments to sort (%lld)", (long long)nseg);
@@ -803,18 +951,18 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
         if (blocks > (int64_t)sms * 16)
             blocks = (int64_t)sms * 16;
         KernelTimer kt_("sort_classify", s);
-        k_classify<<<(unsigned)blocks, 256, 0, s>>>(offsets, nseg, lists.p, nseg, large_tmp.p, hdr.p);
+        k_classify<<<(unsigned)blocks, 256, 0, s>>>(offsets, nseg, lists.p, nseg, large_tmp.p, hdr.p,
+                                                    S, out);
         RT_LAUNCH();
     }
     unsigned long long h[HDR_WORDS];
     RT_CUDA(cudaMemcpyAsync(h, hdr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     RT_CUDA(cudaStreamSynchronize(s));
     auto L = [&](int c) { return lists.p + (int64_t)c * nseg; };
-    uint32_t *u = reinterpret_cast<uint32_t *>(ids);
-    RT_TRY(launch_warp<1>(L(C_W1), (int64_t)h[C_W1], offsets, ids, s));
-    RT_TRY(launch_warp<2>(L(C_W2), (int64_t)h[C_W2], offsets, ids, s));
-    RT_TRY(launch_warp<4>(L(C_W4), (int64_t)h[C_W4], offsets, ids, s));
-    RT_TRY(launch_warp<8>(L(C_W8), (int64_t)h[C_W8], offsets, ids, s));
+    RT_TRY(launch_warp<1>(L(C_W1), (int64_t)h[C_W1], offsets, S, out, s));
+    RT_TRY(launch_warp<2>(L(C_W2), (int64_t)h[C_W2], offsets, S, out, s));
+    RT_TRY(launch_warp<4>(L(C_W4), (int64_t)h[C_W4], offsets, S, out, s));
+    RT_TRY(launch_warp<8>(L(C_W8), (int64_t)h[C_W8], offsets, S, out, s));
     const int64_t n_cta = (int64_t)(h[C_T128] + h[C_T256] + h[C_T512] + h[C_T1024]);
     DevBuf<SegDesc> crowded(s);
     DevBuf<unsigned long long> n_crowded(s);
@@ -822,17 +970,18 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
     RT_TRY(n_crowded.alloc(2, "sort crowded count"));
     RT_CUDA(cudaMemsetAsync(n_crowded.p, 0, 2 * sizeof(unsigned long long), s));
     const Crowded cr1{crowded.p, n_crowded.p, n_cta};
-    RT_TRY((launch_cta<128, false>(L(C_T128), (int64_t)h[C_T128], offsets, u, u, kSign, kSign, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<256, false>(L(C_T256), (int64_t)h[C_T256], offsets, u, u, kSign, kSign, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<512, false>(L(C_T512), (int64_t)h[C_T512], offsets, u, u, kSign, kSign, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<1024, false>(L(C_T1024), (int64_t)h[C_T1024], offsets, u, u, kSign, kSign, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<128, false>(L(C_T128), (int64_t)h[C_T128], offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<256, false>(L(C_T256), (int64_t)h[C_T256], offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<512, false>(L(C_T512), (int64_t)h[C_T512], offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<1024, false>(L(C_T1024), (int64_t)h[C_T1024], offsets, S, nullptr, out, cr1, s, "sort_cta")));
     if (n_cta > 0)
-        RT_TRY(launch_lsd(cr1, u, u, kSign, kSign, s));
+        RT_TRY(launch_lsd(cr1, out, s));
     const int64_t n_large = (int64_t)h[C_LARGE];
     if (n_large == 0)
         return RTREE_OK;
 
-    // Long segments: MSD partition into the scratch area, then sort buckets back.
+    // Long segments: gather into place, MSD-partition into the scratch
+    // area, then sort the buckets back into place.
     const int64_t scratch_n = (int64_t)h[HDR_SCRATCH];
     const int64_t desc_cap = n_large * 2 + 4 * (scratch_n / kCtaMax) + 256;
     DevBuf<uint32_t> scratch(s);
@@ -840,10 +989,16 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
     RT_TRY(scratch.alloc(scratch_n, "sort scratch"));
     RT_TRY(buckets.alloc(desc_cap, "sort buckets"));
     RT_TRY(oversize.alloc(desc_cap, "sort buckets"));
+    const int64_t grid = n_large < (int64_t)sms * 2 ? n_large : (int64_t)sms * 2;
     {
-        int64_t grid = n_large < (int64_t)sms * 2 ? n_large : (int64_t)sms * 2;
+        KernelTimer kt_("sort_gather", s);
+        k_gather_large<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), n_large, offsets, S, out);
+        RT_LAUNCH();
+    }
+    {
         KernelTimer kt_("sort_msd", s);
-        k_msd_partition<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), large_tmp.p, n_large, offsets, u,
+        k_msd_partition<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), large_tmp.p, n_large, offsets,
+                                                        reinterpret_cast<const uint32_t *>(out),
                                                         scratch.p, buckets.p, oversize.p, desc_cap,
                                                         hdr.p);
         RT_LAUNCH();
@@ -857,16 +1012,25 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
     DevBuf<SegDesc> crowded2(s);
     RT_TRY(crowded2.alloc(nb > 0 ? nb : 1, "sort crowded list"));
     const Crowded cr2{crowded2.p, n_crowded.p + 1, nb};
-    RT_TRY((launch_cta<1024, true>(buckets.p, nb, nullptr, scratch.p, u, 0u, kSign, cr2, s, "sort_bucket")));
+    RT_TRY((launch_cta<1024, true>(buckets.p, nb, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
     if (nb > 0)
-        RT_TRY(launch_lsd(cr2, scratch.p, u, 0u, kSign, s));
+        RT_TRY(launch_lsd(cr2, out, s));
     if (no > 0) {
-        int64_t grid = no < (int64_t)sms * 4 ? no : (int64_t)sms * 4;
+        int64_t g2 = no < (int64_t)sms * 4 ? no : (int64_t)sms * 4;
         KernelTimer kt_("sort_global", s);
-        k_sort_global<<<(unsigned)grid, 256, 0, s>>>(oversize.p, no, scratch.p, ids);
+        k_sort_global<<<(unsigned)g2, 256, 0, s>>>(oversize.p, no, scratch.p, out);
         RT_LAUNCH();
     }
     return RTREE_OK;
+}
+
+rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
+                            cudaStream_t s)
+{
+    SortSources S{};
+    S.leaf = ids;
+    S.off_leaf = offsets;
+    return segmented_sort_gather(ids, offsets, nseg, total, S, s);
 }
 
 }  // namespace rt
