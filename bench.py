@@ -160,8 +160,10 @@ def source_sha(files):
 
 
 KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"],
+                  "select_desc": ["select.cu", "internal.cuh"],
                   "select_scatter": ["select.cu", "internal.cuh"],
-                  "sort_mid": ["segsort.cu"], "sort_small": ["segsort.cu"], "sort_large": ["segsort.cu"],
+                  "sort_warp": ["segsort.cu"], "sort_cta": ["segsort.cu"], "sort_gather": ["segsort.cu"],
+                  "sort_msd": ["segsort.cu"], "sort_bucket": ["segsort.cu"],
                   "scatter": ["radix_sort.cu"], "join_count": ["join.cu", "internal.cuh"]}
 
 
@@ -176,24 +178,39 @@ def ncu_traffic(kernel: str):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
         if kv.get("kernel") == kernel and kv.get("workload") == WORKLOAD:
             if kv.get("source_sha") == want:
-                return float(kv["bytes_per_launch"]), kv.get("note")
+                return float(kv["bytes_per_step"]), kv.get("note")
             return None, "kernel changed since the ncu capture"
     return None, None
 
 
 def algorithmic_bytes(stats, F, Q, seg_sizes):
-    """Bytes each kernel must move, per launch (roofline)."""
-    node = F * 16 + 16                     # entry MBRs (all F slots) + node metadata
+    """Bytes each kernel must move in one step (all its launches), from the
+    traversal counters and the per-query result sizes.
+
+    Node visit: F entry MBRs (16 B each, unused slots included) + 16 B of node
+    metadata.  Whole subtree: 16 B metadata read + 8 B (lo, hi) written.  Leaf
+    hit: 4 B id read + 4 B written.  Sorting an id: 4 B gathered + 4 B written
+    (the long-segment path adds three reads and one write for the MSD split).
+    """
+    node = F * 16 + 16
     nodes = stats["nodes_visited"]
-    whole = stats["whole_children"] * 16   # metadata of children taken whole
+    whole = stats["whole_children"]
     hits = stats["ids"]
-    count = nodes * node + whole + Q * (16 + 4)
-    scatter = nodes * node + whole + Q * (16 + 16) + hits * (4 + 4)
-    mid = seg_sizes[(seg_sizes > 32) & (seg_sizes <= 4096)].sum() * 8
-    small = seg_sizes[(seg_sizes > 1) & (seg_sizes <= 32)].sum() * 8
-    large = seg_sizes[seg_sizes > 4096].sum() * 8 * 5
-    return {"select_count": float(count), "select_scatter": float(scatter),
-            "sort_mid": float(mid), "sort_small": float(small), "sort_large": float(large)}
+    leaf_hits = hits - stats["ids_from_whole"]
+    traverse = nodes * node + whole * 16
+    seg = np.asarray(seg_sizes, dtype=np.int64)
+    in_range = lambda lo, hi: int(seg[(seg >= lo) & (seg <= hi)].sum())
+    warp_ids, cta_ids, large_ids = in_range(2, 256), in_range(257, 16384), in_range(16385, 1 << 62)
+    return {
+        "select_count": float(traverse + Q * (16 + 3 * 4)),
+        "select_desc": float(traverse + Q * (16 + 32) + leaf_hits * 8 + whole * 8),
+        "select_scatter": float(traverse + Q * (16 + 16) + hits * 8),
+        "sort_warp": float(warp_ids * 8),
+        "sort_cta": float(cta_ids * 8),
+        "sort_gather": float(large_ids * 8),
+        "sort_msd": float(large_ids * 16),
+        "sort_bucket": float(large_ids * 8),
+    }
 
 
 # ------------------------------------------------------------------- ours
@@ -284,21 +301,24 @@ def run_ours(args):
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
     breakdown = {}
+    total_ms = max(1e-9, sum(v[1] for v in kern.values()))
     for name, (n_l, ms) in kern.items():
         if n_l == 0:
             continue
-        per = ms / n_l
-        entry = {"launches": n_l, "ms_total": round(ms, 3), "share": round(ms / max(1e-9, sum(v[1] for v in kern.values())), 4)}
-        if name in algo and per > 0:
-            entry["gbs"] = round(algo[name] / (per / 1e3) / 1e9, 1)
+        entry = {"launches": n_l, "ms_per_step": round(ms / args.steps, 3),
+                 "share": round(ms / total_ms, 4)}
+        if name in algo and ms > 0:
+            entry["gbs"] = round(algo[name] / (ms / args.steps / 1e3) / 1e9, 1)
         breakdown[name] = entry
     dominant = max((k for k in kern if k in algo), key=lambda k: kern[k][1])
     n_l, ms = kern[dominant]
-    achieved = algo[dominant] / ((ms / n_l) / 1e3) / 1e9
+    ms_step = ms / args.steps  # the kernel's time in one step, all its launches
+    achieved = algo[dominant] / (ms_step / 1e3) / 1e9
     traffic, traffic_note = ncu_traffic(dominant)
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": algo[dominant],
+                "launches_per_step": n_l // args.steps,
+                "algorithmic_bytes_per_step": algo[dominant],
                 "traffic": traffic}
     if traffic_note:
         roofline["traffic_note"] = traffic_note

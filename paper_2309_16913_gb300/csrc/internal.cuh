@@ -222,6 +222,11 @@ struct SelIO {
     const int64_t *off_rng;   // DESC: offsets of the whole-subtree ranges
     int32_t *leaf_out;        // DESC: leaf hits
     int2 *rng_out;            // DESC: (lo, hi) ranges of the tree's id array
+    // Work-queue mapping only: per-query write cursors (zeroed before the
+    // pass), because several warps may emit results for one query.
+    int32_t *cur_ids;         // SCATTER
+    int32_t *cur_leaf;        // DESC
+    int32_t *cur_rng;         // DESC
 };
 
 // Where the ids of segment i come from: leaf[off_leaf[i] .. off_leaf[i+1])
@@ -237,8 +242,10 @@ struct SortSources {
 
 // Writes segment i's ids, sorted ascending (signed), to
 // out[off[i] .. off[i+1]).  out may be the leaf array itself (in place).
+// Enqueues work only (no host synchronization); `total` must bound the sum
+// of all segment lengths.  Device-side capacity problems set bits in *flags.
 rtree_status segmented_sort_gather(int32_t *out, const int64_t *off, int64_t nseg, int64_t total,
-                                   const SortSources &src, cudaStream_t s);
+                                   const SortSources &src, cudaStream_t s, int32_t *flags);
 
 // Sorts every segment ids[offsets[i] .. offsets[i+1]) ascending, in place.
 rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,

@@ -147,13 +147,23 @@ __device__ __forceinline__ void warp_gather(int32_t *__restrict__ sm, const Sort
 }
 
 // ----------------------------------------------------------- warp sorts
+// Device-resident list lengths: kernels launched without a host round trip
+// read how many entries to process.
+__device__ __forceinline__ int64_t list_len(const unsigned long long *count, int64_t cap)
+{
+    const int64_t c = (int64_t)*count;
+    return c < cap ? c : cap;
+}
+
 // Bitonic sort of up to 32*K signed ids; element e = k*32 + lane (striped).
 template <int K>
-__global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ list, int64_t cnt,
-                                                   const int64_t *__restrict__ off, SortSources S,
-                                                   int32_t *__restrict__ out)
+__global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ list,
+                                                   const unsigned long long *__restrict__ count,
+                                                   int64_t cap, const int64_t *__restrict__ off,
+                                                   SortSources S, int32_t *__restrict__ out)
 {
     constexpr int N = 32 * K;
+    const int64_t cnt = list_len(count, cap);
     __shared__ int32_t stage[8][N];
     const int lane = threadIdx.x & 31;
     int32_t *sm = stage[threadIdx.x >> 5];
@@ -451,13 +461,15 @@ __device__ __forceinline__ void push_crowded(SegDesc *list, unsigned long long *
 // keys sit in `scratch`; otherwise segment ids whose ids are gathered from S.
 template <int THREADS, bool BUCKETS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-    k_sort_cta(const void *__restrict__ list, int64_t cnt, const int64_t *__restrict__ off,
-               SortSources S, const uint32_t *__restrict__ scratch, int32_t *__restrict__ out,
+    k_sort_cta(const void *__restrict__ list, const unsigned long long *__restrict__ count,
+               int64_t list_cap, const int64_t *__restrict__ off, SortSources S,
+               const uint32_t *__restrict__ scratch, int32_t *__restrict__ out,
                SegDesc *__restrict__ crowded, unsigned long long *__restrict__ n_crowded,
                int64_t crowded_cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem<THREADS> &sm = *reinterpret_cast<CtaSmem<THREADS> *>(smem_raw);
+    const int64_t cnt = list_len(count, list_cap);
     for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
         int64_t dof;
         int n;
@@ -619,15 +631,19 @@ __global__ void __launch_bounds__(1024, 1)
 // ------------------------------------------------------------ MSD step
 // Gathers each long segment into its place in `out` (unsorted).
 __global__ void __launch_bounds__(1024)
-    k_gather_large(const int32_t *__restrict__ list, int64_t cnt, const int64_t *__restrict__ off,
-                   SortSources S, int32_t *__restrict__ out)
+    k_gather_large(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
+                   int64_t list_cap, const int64_t *__restrict__ tmp_off, int64_t scratch_cap,
+                   const int64_t *__restrict__ off, SortSources S, int32_t *__restrict__ out)
 {
+    const int64_t cnt = list_len(count, list_cap);
     __shared__ int32_t rstart[1024];
     __shared__ int32_t wsum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
         const int32_t i = list[b];
         int32_t *dst = out + off[i];
+        if (tmp_off[b] + (off[i + 1] - off[i]) > scratch_cap)
+            continue;  // over the scratch capacity: reported by k_msd_partition
         const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
         if (S.leaf + l0 != dst)
             for (int64_t e = l0 + threadIdx.x; e < l1; e += 1024)
@@ -679,11 +695,13 @@ __global__ void __launch_bounds__(1024)
 // for the global LSD fallback).
 __global__ void __launch_bounds__(1024)
     k_msd_partition(const int32_t *__restrict__ list, const int64_t *__restrict__ tmp_off,
-                    int64_t cnt, const int64_t *__restrict__ off, const uint32_t *__restrict__ ids,
-                    uint32_t *__restrict__ scratch, SegDesc *__restrict__ buckets,
-                    SegDesc *__restrict__ oversize, int64_t desc_cap,
-                    unsigned long long *__restrict__ hdr)
+                    const unsigned long long *__restrict__ count, int64_t list_cap,
+                    int64_t scratch_cap, const int64_t *__restrict__ off,
+                    const uint32_t *__restrict__ ids, uint32_t *__restrict__ scratch,
+                    SegDesc *__restrict__ buckets, SegDesc *__restrict__ oversize, int64_t desc_cap,
+                    unsigned long long *__restrict__ hdr, int32_t *__restrict__ flags)
 {
+    const int64_t cnt = list_len(count, list_cap);
     __shared__ uint32_t hist[kBins], cursor[kBins];
     __shared__ uint32_t red_and[32], red_or[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -692,6 +710,11 @@ __global__ void __launch_bounds__(1024)
         const int64_t o = off[seg];
         const int64_t n = off[seg + 1] - o;
         const int64_t t = tmp_off[b];
+        if (t + n > scratch_cap) {  // cannot happen when the scratch holds all ids
+            if (threadIdx.x == 0)
+                atomicOr(flags, 1);
+            continue;
+        }
         uint32_t a_and = 0xffffffffu, a_or = 0;
         for (int64_t p = threadIdx.x; p < n; p += 1024) {
             const uint32_t k = ids[o + p] ^ kSign;
@@ -759,10 +782,14 @@ __global__ void __launch_bounds__(1024)
                 const unsigned long long slot = atomicAdd(hdr + HDR_BUCKETS, 1ull);
                 if ((int64_t)slot < desc_cap)
                     buckets[slot] = s;
+                else
+                    atomicOr(flags, 2);
             } else {
                 const unsigned long long slot = atomicAdd(hdr + HDR_OVERSIZE, 1ull);
                 if ((int64_t)slot < desc_cap)
                     oversize[slot] = s;
+                else
+                    atomicOr(flags, 2);
             }
         }
         __syncthreads();
@@ -779,9 +806,10 @@ __global__ void __launch_bounds__(1024)
 // sort through global memory from the bucket's scratch range (keys) to its
 // place in the output, ping-ponging between the two.
 __global__ void __launch_bounds__(256)
-    k_sort_global(const SegDesc *__restrict__ list, int64_t cnt, uint32_t *__restrict__ scratch,
-                  int32_t *__restrict__ ids)
+    k_sort_global(const SegDesc *__restrict__ list, const unsigned long long *__restrict__ count,
+                  int64_t list_cap, uint32_t *__restrict__ scratch, int32_t *__restrict__ ids)
 {
+    const int64_t cnt = list_len(count, list_cap);
     __shared__ uint32_t hist[kBins], run[kBins];
     __shared__ uint32_t red_and[8], red_or[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -882,11 +910,11 @@ struct Crowded {
 };
 
 template <int THREADS, bool BUCKETS>
-rtree_status launch_cta(const void *list, int64_t cnt, const int64_t *off, const SortSources &S,
-                        const uint32_t *scratch, int32_t *out, const Crowded &cr, cudaStream_t s,
-                        const char *name)
+rtree_status launch_cta(const void *list, const unsigned long long *count, int64_t list_cap,
+                        const int64_t *off, const SortSources &S, const uint32_t *scratch,
+                        int32_t *out, const Crowded &cr, cudaStream_t s, const char *name)
 {
-    if (cnt <= 0)
+    if (list_cap <= 0)
         return RTREE_OK;
     auto kern = k_sort_cta<THREADS, BUCKETS>;
     const size_t bytes = sizeof(CtaSmem<THREADS>);
@@ -894,17 +922,19 @@ rtree_status launch_cta(const void *list, int64_t cnt, const int64_t *off, const
     int per_sm = 0;
     RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, bytes));
     int64_t grid = (int64_t)(per_sm > 0 ? per_sm : 1) * sm_count();
-    if (grid > cnt)
-        grid = cnt;
+    if (grid > list_cap)
+        grid = list_cap;
     KernelTimer kt_(name, s);
-    kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, cnt, off, S, scratch, out, cr.list, cr.count,
-                                                cr.cap);
+    kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, count, list_cap, off, S, scratch, out, cr.list,
+                                                cr.count, cr.cap);
     RT_LAUNCH();
     return RTREE_OK;
 }
 
 rtree_status launch_lsd(const Crowded &cr, int32_t *out, cudaStream_t s)
 {
+    if (cr.cap <= 0)
+        return RTREE_OK;
     const size_t bytes = sizeof(CtaSmem<1024>);
     RT_TRY(set_smem(k_sort_lsd, bytes));
     KernelTimer kt_("sort_lsd", s);
@@ -914,17 +944,17 @@ rtree_status launch_lsd(const Crowded &cr, int32_t *out, cudaStream_t s)
 }
 
 template <int K>
-rtree_status launch_warp(const int32_t *list, int64_t cnt, const int64_t *off, const SortSources &S,
-                         int32_t *out, cudaStream_t s)
+rtree_status launch_warp(const int32_t *list, const unsigned long long *count, int64_t list_cap,
+                         const int64_t *off, const SortSources &S, int32_t *out, cudaStream_t s)
 {
-    if (cnt <= 0)
+    if (list_cap <= 0)
         return RTREE_OK;
-    int64_t blocks = (cnt + 7) / 8;
+    int64_t blocks = (list_cap + 7) / 8;
     const int64_t cap = (int64_t)sm_count() * 16;
     if (blocks > cap)
         blocks = cap;
     KernelTimer kt_("sort_warp", s);
-    k_sort_warp<K><<<(unsigned)blocks, 256, 0, s>>>(list, cnt, off, S, out);
+    k_sort_warp<K><<<(unsigned)blocks, 256, 0, s>>>(list, count, list_cap, off, S, out);
     RT_LAUNCH();
     return RTREE_OK;
 }
@@ -932,19 +962,25 @@ rtree_status launch_warp(const int32_t *list, int64_t cnt, const int64_t *off, c
 }  // namespace
 
 rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t nseg, int64_t total,
-                                   const SortSources &S, cudaStream_t s)
+                                   const SortSources &S, cudaStream_t s, int32_t *flags)
 {
     if (nseg <= 0 || total <= 0)
         return RTREE_OK;
     if (nseg >= (int64_t)INT32_MAX)
         return fail(RTREE_EOVERFLOW, "too many segments to sort (%lld)", (long long)nseg);
+    // Every list length stays on the device; the launches below are sized
+    // by upper bounds and read the actual lengths themselves, so the whole
+    // sort is enqueued without a host round trip.
+    const int64_t max_large = total / (kCtaMax + 1) + 1 < nseg ? total / (kCtaMax + 1) + 1 : nseg;
+    const int64_t scratch_cap = total;
+    const int64_t desc_cap = 2 * max_large + 4 * (scratch_cap / kCtaMax) + 256;
     DevBuf<int32_t> lists(s);
     DevBuf<int64_t> large_tmp(s);
     DevBuf<unsigned long long> hdr(s);
     RT_TRY(lists.alloc((size_t)C_COUNT * nseg, "sort lists"));
     RT_TRY(large_tmp.alloc(nseg, "sort lists"));
-    RT_TRY(hdr.alloc(HDR_WORDS, "sort counters"));
-    RT_CUDA(cudaMemsetAsync(hdr.p, 0, HDR_WORDS * sizeof(unsigned long long), s));
+    RT_TRY(hdr.alloc(HDR_WORDS + 2, "sort counters"));
+    RT_CUDA(cudaMemsetAsync(hdr.p, 0, (HDR_WORDS + 2) * sizeof(unsigned long long), s));
     const int sms = sm_count();
     {
         int64_t blocks = (nseg + 255) / 256;
@@ -955,70 +991,58 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
                                                     S, out);
         RT_LAUNCH();
     }
-    unsigned long long h[HDR_WORDS];
-    RT_CUDA(cudaMemcpyAsync(h, hdr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
     auto L = [&](int c) { return lists.p + (int64_t)c * nseg; };
-    RT_TRY(launch_warp<1>(L(C_W1), (int64_t)h[C_W1], offsets, S, out, s));
-    RT_TRY(launch_warp<2>(L(C_W2), (int64_t)h[C_W2], offsets, S, out, s));
-    RT_TRY(launch_warp<4>(L(C_W4), (int64_t)h[C_W4], offsets, S, out, s));
-    RT_TRY(launch_warp<8>(L(C_W8), (int64_t)h[C_W8], offsets, S, out, s));
-    const int64_t n_cta = (int64_t)(h[C_T128] + h[C_T256] + h[C_T512] + h[C_T1024]);
+    auto H = [&](int c) { return hdr.p + c; };
+    // a class can hold at most total / (its smallest length) segments
+    auto cap_of = [&](int64_t min_len) { return total / min_len < nseg ? total / min_len : nseg; };
+    RT_TRY(launch_warp<1>(L(C_W1), H(C_W1), cap_of(2), offsets, S, out, s));
+    RT_TRY(launch_warp<2>(L(C_W2), H(C_W2), cap_of(33), offsets, S, out, s));
+    RT_TRY(launch_warp<4>(L(C_W4), H(C_W4), cap_of(65), offsets, S, out, s));
+    RT_TRY(launch_warp<8>(L(C_W8), H(C_W8), cap_of(129), offsets, S, out, s));
+    const int64_t cta_cap = cap_of(257);
     DevBuf<SegDesc> crowded(s);
-    DevBuf<unsigned long long> n_crowded(s);
-    RT_TRY(crowded.alloc(n_cta > 0 ? n_cta : 1, "sort crowded list"));
-    RT_TRY(n_crowded.alloc(2, "sort crowded count"));
-    RT_CUDA(cudaMemsetAsync(n_crowded.p, 0, 2 * sizeof(unsigned long long), s));
-    const Crowded cr1{crowded.p, n_crowded.p, n_cta};
-    RT_TRY((launch_cta<128, false>(L(C_T128), (int64_t)h[C_T128], offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<256, false>(L(C_T256), (int64_t)h[C_T256], offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<512, false>(L(C_T512), (int64_t)h[C_T512], offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<1024, false>(L(C_T1024), (int64_t)h[C_T1024], offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    if (n_cta > 0)
-        RT_TRY(launch_lsd(cr1, out, s));
-    const int64_t n_large = (int64_t)h[C_LARGE];
-    if (n_large == 0)
-        return RTREE_OK;
+    RT_TRY(crowded.alloc(cta_cap > 0 ? cta_cap : 1, "sort crowded list"));
+    unsigned long long *n_crowded = hdr.p + HDR_WORDS;  // two counters after the header
+    const Crowded cr1{crowded.p, n_crowded, cta_cap};
+    RT_TRY((launch_cta<128, false>(L(C_T128), H(C_T128), cap_of(257), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<256, false>(L(C_T256), H(C_T256), cap_of(2049), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<512, false>(L(C_T512), H(C_T512), cap_of(4097), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<1024, false>(L(C_T1024), H(C_T1024), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY(launch_lsd(cr1, out, s));
+    if (total <= kCtaMax)
+        return RTREE_OK;  // no segment can be long
 
-    // Long segments: gather into place, MSD-partition into the scratch
-    // area, then sort the buckets back into place.
-    const int64_t scratch_n = (int64_t)h[HDR_SCRATCH];
-    const int64_t desc_cap = n_large * 2 + 4 * (scratch_n / kCtaMax) + 256;
+    // Long segments: gather into place, MSD-partition into the scratch area,
+    // then sort the buckets back into place.
     DevBuf<uint32_t> scratch(s);
-    DevBuf<SegDesc> buckets(s), oversize(s);
-    RT_TRY(scratch.alloc(scratch_n, "sort scratch"));
+    DevBuf<SegDesc> buckets(s), oversize(s), crowded2(s);
+    RT_TRY(scratch.alloc(scratch_cap, "sort scratch"));
     RT_TRY(buckets.alloc(desc_cap, "sort buckets"));
     RT_TRY(oversize.alloc(desc_cap, "sort buckets"));
-    const int64_t grid = n_large < (int64_t)sms * 2 ? n_large : (int64_t)sms * 2;
+    RT_TRY(crowded2.alloc(desc_cap, "sort crowded list"));
+    const int64_t grid = max_large < (int64_t)sms * 2 ? max_large : (int64_t)sms * 2;
     {
         KernelTimer kt_("sort_gather", s);
-        k_gather_large<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), n_large, offsets, S, out);
+        k_gather_large<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), H(C_LARGE), max_large, large_tmp.p,
+                                                       scratch_cap, offsets, S, out);
         RT_LAUNCH();
     }
     {
         KernelTimer kt_("sort_msd", s);
-        k_msd_partition<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), large_tmp.p, n_large, offsets,
-                                                        reinterpret_cast<const uint32_t *>(out),
-                                                        scratch.p, buckets.p, oversize.p, desc_cap,
-                                                        hdr.p);
+        k_msd_partition<<<(unsigned)grid, 1024, 0, s>>>(
+            L(C_LARGE), large_tmp.p, H(C_LARGE), max_large, scratch_cap, offsets,
+            reinterpret_cast<const uint32_t *>(out), scratch.p, buckets.p, oversize.p, desc_cap,
+            hdr.p, flags);
         RT_LAUNCH();
     }
-    RT_CUDA(cudaMemcpyAsync(h, hdr.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
-    const int64_t nb = (int64_t)h[HDR_BUCKETS], no = (int64_t)h[HDR_OVERSIZE];
-    if (nb > desc_cap || no > desc_cap)
-        return fail(RTREE_EINTERNAL, "sort bucket list overflow (%lld, %lld > %lld)", (long long)nb,
-                    (long long)no, (long long)desc_cap);
-    DevBuf<SegDesc> crowded2(s);
-    RT_TRY(crowded2.alloc(nb > 0 ? nb : 1, "sort crowded list"));
-    const Crowded cr2{crowded2.p, n_crowded.p + 1, nb};
-    RT_TRY((launch_cta<1024, true>(buckets.p, nb, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
-    if (nb > 0)
-        RT_TRY(launch_lsd(cr2, out, s));
-    if (no > 0) {
-        int64_t g2 = no < (int64_t)sms * 4 ? no : (int64_t)sms * 4;
+    const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
+    RT_TRY((launch_cta<1024, true>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
+    RT_TRY(launch_lsd(cr2, out, s));
+    {
+        int64_t g2 = desc_cap < (int64_t)sms * 4 ? desc_cap : (int64_t)sms * 4;
         KernelTimer kt_("sort_global", s);
-        k_sort_global<<<(unsigned)g2, 256, 0, s>>>(oversize.p, no, scratch.p, out);
+        k_sort_global<<<(unsigned)g2, 256, 0, s>>>(oversize.p, H(HDR_OVERSIZE), desc_cap, scratch.p,
+                                                   out);
         RT_LAUNCH();
     }
     return RTREE_OK;
@@ -1030,7 +1054,10 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
     SortSources S{};
     S.leaf = ids;
     S.off_leaf = offsets;
-    return segmented_sort_gather(ids, offsets, nseg, total, S, s);
+    DevBuf<int32_t> flags(s);
+    RT_TRY(flags.alloc(1, "sort flags"));
+    RT_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int32_t), s));
+    return segmented_sort_gather(ids, offsets, nseg, total, S, s, flags.p);
 }
 
 }  // namespace rt

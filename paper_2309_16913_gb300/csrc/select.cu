@@ -22,6 +22,10 @@
 // entries) without being visited, and the output is produced in two passes
 // over the same traversal: count, exclusive scan, scatter at the offsets.
 //
+// Mappings: warp per query (a warp takes the next query from a counter and
+// walks its whole subtree), or a persistent device work queue of (query,
+// node) items from which warps split large queries (k_select_wq below).
+//
 // Pass kinds:
 //   COUNT    per query: ids found, and (optionally) how many came one by one
 //            from leaves and how many whole subtrees were taken;
@@ -37,7 +41,7 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 enum { PASS_COUNT = 0, PASS_SCATTER = 1, PASS_DESC = 2 };
-enum { FLAG_STACK = 1, FLAG_COUNT_MISMATCH = 2 };
+enum { FLAG_STACK = 1, FLAG_COUNT_MISMATCH = 2, FLAG_TIMEOUT = 4 };
 
 // Copies ids[lo, hi) to out[0, hi-lo) with the whole warp.
 __device__ __forceinline__ void warp_copy(int32_t *__restrict__ out,
@@ -57,15 +61,164 @@ __device__ __forceinline__ void warp_copy(int32_t *__restrict__ out,
         out[e - lo] = __ldg(ids + e);
 }
 
+// Results of one walk (a query, or one (query, subtree) work item).
+struct Walk {
+    int64_t cur;   // ids found, warp-uniform
+    int64_t lcur;  // of which found one by one in leaves
+    int64_t rcur;  // whole subtrees taken
+    unsigned long long n_visit, n_leaf;
+    bool overflow;
+};
+
+// Output limits of one query (non-work-queue passes write at fixed offsets).
+struct Seg {
+    int64_t base, lim, lbase, llim, rbase, rlim;
+};
+
+// Reserves n slots of a per-query cursor (lane 0 does the atomic).
+__device__ __forceinline__ int64_t reserve(int32_t *cursor, int n, int lane)
+{
+    int r = 0;
+    if (lane == 0 && n > 0)
+        r = atomicAdd(cursor, n);
+    return __shfl_sync(RT_FULL, r, 0);
+}
+
+// One step of a walk: pops up to K nodes from the warp's stack, tests their
+// children against the query (ballot), pushes children that need a visit,
+// and emits leaf hits and whole subtrees.  WQ: output slots are reserved from
+// per-query cursors (several warps may serve one query); otherwise they
+// follow the walk's own counters from the query's segment start.
+template <int F, int LAYOUT, int PASS, bool WQ>
+__device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, int32_t *st, int &top,
+                                            int cap, const SelIO &io, int64_t qi, const Seg &sg,
+                                            Walk &wk, bool stats, int lane, int grp, int sub,
+                                            unsigned lt)
+{
+    constexpr int G = F < 32 ? F : 32;
+    constexpr int K = 32 / G;
+    constexpr int C = F / G;
+    const int k = top < K ? top : K;
+    const int node = grp < k ? st[top - 1 - grp] : -1;
+    top -= k;
+    __syncwarp();
+    if (stats) {
+        wk.n_visit += k;
+        wk.n_leaf += __popc(__ballot_sync(RT_FULL, node >= t.leaf_base && sub == 0));
+    }
+    // Entry loads do not wait for the node's metadata: unused slots hold the
+    // empty box, and the count only masks them afterwards.
+    float4 b[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        b[c] = node >= 0 ? load_entry_t<F, LAYOUT>(t.mbr, node, sub + c * G) : empty_box();
+    const int4 m = node >= 0 ? __ldg(t.meta + node) : make_int4(0, 0, 0, 0);
+    const bool leaf = node >= t.leaf_base;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int j = sub + c * G;
+        const bool hit = node >= 0 && j < m.y && meets(b[c], q);
+        const bool cont = hit && !leaf && inside(b[c], q);
+        const bool push = hit && !leaf && !cont;
+        const bool emit = hit && leaf;
+        const unsigned mp = __ballot_sync(RT_FULL, push);
+        if (push) {
+            const int pos = top + __popc(mp & lt);
+            if (pos < cap)
+                st[pos] = m.x + j;
+        }
+        top += __popc(mp);
+        const unsigned me = __ballot_sync(RT_FULL, emit);
+        if (PASS == PASS_SCATTER && me) {
+            const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, __popc(me), lane) : sg.base + wk.cur;
+            const int64_t o = at + __popc(me & lt);
+            if (emit && o < sg.lim)
+                io.out[o] = __ldg(t.ids + m.x + j);
+        }
+        if (PASS == PASS_DESC && me) {
+            const int64_t at = WQ ? sg.lbase + reserve(io.cur_leaf + qi, __popc(me), lane) : sg.lbase + wk.lcur;
+            const int64_t o = at + __popc(me & lt);
+            if (emit && o < sg.llim)
+                io.leaf_out[o] = __ldg(t.ids + m.x + j);
+        }
+        wk.cur += __popc(me);
+        wk.lcur += __popc(me);
+        const unsigned mc = __ballot_sync(RT_FULL, cont);
+        if (mc) {
+            int lo = 0, hi = 0;
+            if (cont) {
+                const int4 cm = __ldg(t.meta + m.x + j);
+                lo = cm.z;
+                hi = cm.w;
+            }
+            if (PASS == PASS_DESC) {
+                const int64_t at = WQ ? sg.rbase + reserve(io.cur_rng + qi, __popc(mc), lane) : sg.rbase + wk.rcur;
+                const int64_t o = at + __popc(mc & lt);
+                if (cont && o < sg.rlim)
+                    io.rng_out[o] = make_int2(lo, hi);
+            }
+            wk.rcur += __popc(mc);
+            if (PASS == PASS_SCATTER) {
+                unsigned mm = mc;
+                while (mm) {
+                    const int src = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    const int l = __shfl_sync(RT_FULL, lo, src);
+                    const int h = __shfl_sync(RT_FULL, hi, src);
+                    const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, h - l, lane) : sg.base + wk.cur;
+                    const int64_t room = sg.lim - at;
+                    const int hh = (int64_t)(h - l) <= room ? h : l + (int)(room > 0 ? room : 0);
+                    warp_copy(io.out + at, t.ids, l, hh, lane);
+                    wk.cur += h - l;
+                }
+            } else {
+                wk.cur += __reduce_add_sync(RT_FULL, (unsigned)(hi - lo));
+            }
+        }
+    }
+    if (top > cap) {  // cannot happen with cap = H*max(32,F); guarded anyway
+        wk.overflow = true;
+        top = 0;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ Seg seg_of(const SelIO &io, int pass, int64_t qi)
+{
+    Seg sg{0, 0, 0, 0, 0, 0};
+    if (pass == PASS_SCATTER) {
+        sg.base = __ldg(io.offsets + qi);
+        sg.lim = __ldg(io.offsets + qi + 1);  // writes never pass the segment end
+    }
+    if (pass == PASS_DESC) {
+        sg.lbase = __ldg(io.off_leaf + qi);
+        sg.llim = __ldg(io.off_leaf + qi + 1);
+        sg.rbase = __ldg(io.off_rng + qi);
+        sg.rlim = __ldg(io.off_rng + qi + 1);
+    }
+    return sg;
+}
+
+__device__ __forceinline__ void flush_stats(unsigned long long *stats, const Walk &wk, bool new_query)
+{
+    if (new_query)
+        atomicAdd(stats + 0, 1ull);
+    atomicAdd(stats + 1, wk.n_visit);
+    atomicAdd(stats + 2, wk.n_leaf);
+    atomicAdd(stats + 3, (unsigned long long)wk.rcur);
+    atomicAdd(stats + 4, (unsigned long long)wk.cur);
+    atomicAdd(stats + 5, (unsigned long long)(wk.cur - wk.lcur));
+}
+
+// Warp per query: each warp takes the next query from a counter and walks
+// its whole subtree.
 template <int F, int LAYOUT, int PASS>
 __global__ void __launch_bounds__(kThreads)
     k_select(TreeDev t, const float4 *__restrict__ queries, int64_t Q, SelIO io,
              unsigned long long *__restrict__ next_query, int32_t *__restrict__ flags, int cap,
              unsigned long long *__restrict__ stats)
 {
-    constexpr int G = F < 32 ? F : 32;  // lanes per node
-    constexpr int K = 32 / G;           // nodes per warp step
-    constexpr int C = F / G;            // children per lane
+    constexpr int G = F < 32 ? F : 32;
     extern __shared__ int32_t smem[];
     const int lane = threadIdx.x & 31;
     int32_t *st = smem + (threadIdx.x >> 5) * cap;
@@ -80,21 +233,8 @@ __global__ void __launch_bounds__(kThreads)
         if (qi >= (unsigned long long)Q)
             break;
         const float4 q = __ldg(queries + qi);
-        // output cursors: ids (SCATTER), leaf hits and ranges (DESC)
-        int64_t base = 0, lim = 0, lbase = 0, llim = 0, rbase = 0, rlim = 0;
-        if (PASS == PASS_SCATTER) {
-            base = __ldg(io.offsets + qi);
-            lim = __ldg(io.offsets + qi + 1);  // writes never pass the segment end
-        }
-        if (PASS == PASS_DESC) {
-            lbase = __ldg(io.off_leaf + qi);
-            llim = __ldg(io.off_leaf + qi + 1);
-            rbase = __ldg(io.off_rng + qi);
-            rlim = __ldg(io.off_rng + qi + 1);
-        }
-        int64_t cur = 0;   // ids found so far, warp-uniform
-        int64_t lcur = 0;  // leaf hits so far
-        int64_t rcur = 0;  // whole subtrees so far
+        const Seg sg = seg_of(io, PASS, (int64_t)qi);
+        Walk wk{0, 0, 0, 0, 0, false};
         int top = 0;
         if (t.nodes > 0) {
             if (lane == 0)
@@ -102,119 +242,213 @@ __global__ void __launch_bounds__(kThreads)
             top = 1;
         }
         __syncwarp();
-        bool overflow = false;
-        unsigned long long n_visit = 0, n_leaf = 0;
         int steps = 0;  // a query visits each node at most once
         while (top > 0) {
             if (++steps > t.nodes) {
-                overflow = true;
+                wk.overflow = true;
                 break;
             }
-            const int k = top < K ? top : K;
-            const int node = grp < k ? st[top - 1 - grp] : -1;
-            top -= k;
-            __syncwarp();
-            if (stats) {
-                n_visit += k;
-                n_leaf += __popc(__ballot_sync(RT_FULL, node >= t.leaf_base && sub == 0));
-            }
-            // Entry loads do not wait for the node's metadata: unused slots
-            // hold the empty box, and the count only masks them afterwards.
-            float4 b[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                b[c] = node >= 0 ? load_entry_t<F, LAYOUT>(t.mbr, node, sub + c * G) : empty_box();
-            const int4 m = node >= 0 ? __ldg(t.meta + node) : make_int4(0, 0, 0, 0);
-            const bool leaf = node >= t.leaf_base;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const int j = sub + c * G;
-                const bool hit = node >= 0 && j < m.y && meets(b[c], q);
-                const bool cont = hit && !leaf && inside(b[c], q);
-                const bool push = hit && !leaf && !cont;
-                const bool emit = hit && leaf;
-                const unsigned mp = __ballot_sync(RT_FULL, push);
-                if (push) {
-                    const int pos = top + __popc(mp & lt);
-                    if (pos < cap)
-                        st[pos] = m.x + j;
-                }
-                top += __popc(mp);
-                const unsigned me = __ballot_sync(RT_FULL, emit);
-                if (PASS == PASS_SCATTER && emit) {
-                    const int64_t o = base + cur + __popc(me & lt);
-                    if (o < lim)
-                        io.out[o] = __ldg(t.ids + m.x + j);
-                }
-                if (PASS == PASS_DESC && emit) {
-                    const int64_t o = lbase + lcur + __popc(me & lt);
-                    if (o < llim)
-                        io.leaf_out[o] = __ldg(t.ids + m.x + j);
-                }
-                cur += __popc(me);
-                lcur += __popc(me);
-                const unsigned mc = __ballot_sync(RT_FULL, cont);
-                if (mc) {
-                    int lo = 0, hi = 0;
-                    if (cont) {
-                        const int4 cm = __ldg(t.meta + m.x + j);
-                        lo = cm.z;
-                        hi = cm.w;
-                    }
-                    if (PASS == PASS_DESC && cont) {
-                        const int64_t o = rbase + rcur + __popc(mc & lt);
-                        if (o < rlim)
-                            io.rng_out[o] = make_int2(lo, hi);
-                    }
-                    rcur += __popc(mc);
-                    if (PASS == PASS_SCATTER) {
-                        unsigned mm = mc;
-                        while (mm) {
-                            const int src = __ffs(mm) - 1;
-                            mm &= mm - 1;
-                            const int l = __shfl_sync(RT_FULL, lo, src);
-                            const int h = __shfl_sync(RT_FULL, hi, src);
-                            const int64_t room = lim - (base + cur);
-                            const int hh = (int64_t)(h - l) <= room ? h : l + (int)(room > 0 ? room : 0);
-                            warp_copy(io.out + base + cur, t.ids, l, hh, lane);
-                            cur += h - l;
-                        }
-                    } else {
-                        cur += __reduce_add_sync(RT_FULL, (unsigned)(hi - lo));
-                    }
-                }
-            }
-            if (top > cap) {  // cannot happen with cap = H*max(32,F); guarded anyway
-                overflow = true;
-                top = 0;
-            }
-            __syncwarp();
+            select_step<F, LAYOUT, PASS, false>(t, q, st, top, cap, io, (int64_t)qi, sg, wk,
+                                                stats != nullptr, lane, grp, sub, lt);
         }
-        if (stats && lane == 0) {
-            atomicAdd(stats + 0, 1ull);
-            atomicAdd(stats + 1, n_visit);
-            atomicAdd(stats + 2, n_leaf);
-            atomicAdd(stats + 3, (unsigned long long)rcur);
-            atomicAdd(stats + 4, (unsigned long long)cur);
-            atomicAdd(stats + 5, (unsigned long long)(cur - lcur));
-        }
+        if (stats && lane == 0)
+            flush_stats(stats, wk, true);
         if (lane == 0) {
-            if (overflow)
+            if (wk.overflow)
                 atomicOr(flags, FLAG_STACK);
             if (PASS == PASS_COUNT) {
-                io.counts[qi] = (int32_t)cur;
+                io.counts[qi] = (int32_t)wk.cur;
                 if (io.counts_leaf)
-                    io.counts_leaf[qi] = (int32_t)lcur;
+                    io.counts_leaf[qi] = (int32_t)wk.lcur;
                 if (io.counts_rng)
-                    io.counts_rng[qi] = (int32_t)rcur;
+                    io.counts_rng[qi] = (int32_t)wk.rcur;
             } else if (PASS == PASS_SCATTER) {
-                if (cur != lim - base)
+                if (wk.cur != sg.lim - sg.base)
                     atomicOr(flags, FLAG_COUNT_MISMATCH);
             } else {
-                if (lcur != llim - lbase || rcur != rlim - rbase)
+                if (wk.lcur != sg.llim - sg.lbase || wk.rcur != sg.rlim - sg.rbase)
                     atomicOr(flags, FLAG_COUNT_MISMATCH);
             }
         }
+    }
+}
+
+// ------------------------------------------------- persistent work queue
+// Device work queue of (query, node) items, each published as one 64-bit
+// word (query in the low half, node in the high half; all ones = empty).
+// Slots [0, Q) start as (q, root); the others are filled by donations.  A
+// warp takes a ticket (head++) and waits for that slot to be filled, or for
+// `pending` (items not yet finished) to reach zero, which ends the pass.  A
+// warp whose stack holds two or more entries while other warps wait
+// (head > tail) donates the older half of its stack (the nodes nearest the
+// root, i.e. the largest subtrees) to new slots.  pending cannot reach zero
+// while a donor runs, because the donor's own item is still pending.  Waits
+// are bounded: past kWaitCycles the warp sets FLAG_TIMEOUT and leaves (the
+// host reports RTREE_ETIMEOUT).
+struct WorkQueue {
+    unsigned long long *items;
+    long long cap;
+    unsigned long long *head;
+    unsigned long long *tail;
+    long long *pending;
+};
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr long long kWaitCycles = 2000000000LL;  // about one second
+
+__device__ __forceinline__ unsigned long long pack_item(int q, int node)
+{
+    return (unsigned long long)(unsigned)q | ((unsigned long long)(unsigned)node << 32);
+}
+
+template <int F, int LAYOUT, int PASS>
+__global__ void __launch_bounds__(kThreads)
+    k_select_wq(TreeDev t, const float4 *__restrict__ queries, int64_t Q, SelIO io, WorkQueue wq,
+                int32_t *__restrict__ flags, int cap, unsigned long long *__restrict__ stats)
+{
+    constexpr int G = F < 32 ? F : 32;
+    extern __shared__ int32_t smem[];
+    const int lane = threadIdx.x & 31;
+    int32_t *st = smem + (threadIdx.x >> 5) * cap;
+    const int grp = lane / G, sub = lane % G;
+    const unsigned lt = lanemask_lt();
+
+    for (;;) {
+        unsigned long long ticket = 0;
+        if (lane == 0)
+            ticket = atomicAdd(wq.head, 1ull);
+        ticket = __shfl_sync(RT_FULL, ticket, 0);
+        if ((long long)ticket >= wq.cap)
+            return;
+        // wait for the slot to be filled (or for the pass to end)
+        unsigned long long word = kEmpty;
+        if (lane == 0) {
+            const long long t0 = clock64();
+            const volatile unsigned long long *slot = wq.items + ticket;
+            const volatile long long *pend = wq.pending;
+            unsigned ns = 32;
+            for (;;) {
+                word = *slot;
+                if (word != kEmpty)
+                    break;
+                if (*pend == 0)
+                    break;
+                if (clock64() - t0 > kWaitCycles) {
+                    atomicOr(flags, FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 2048)
+                    ns <<= 1;
+            }
+            __threadfence();
+        }
+        word = __shfl_sync(RT_FULL, word, 0);
+        if (word == kEmpty)
+            return;
+        const int64_t qi = (int64_t)(unsigned)(word & 0xffffffffull);
+        const int root = (int)(word >> 32);
+        const float4 q = __ldg(queries + qi);
+        const Seg sg = seg_of(io, PASS, qi);
+        Walk wk{0, 0, 0, 0, 0, false};
+        if (lane == 0)
+            st[0] = root;
+        int top = 1;
+        __syncwarp();
+        int steps = 0;
+        while (top > 0) {
+            if (++steps > t.nodes) {
+                wk.overflow = true;
+                break;
+            }
+            select_step<F, LAYOUT, PASS, true>(t, q, st, top, cap, io, qi, sg, wk,
+                                               stats != nullptr, lane, grp, sub, lt);
+            // donate the older half of the stack when other warps are waiting
+            if (top >= 2 && (steps & 3) == 0) {
+                unsigned long long h = 0, tl = 0;
+                if (lane == 0) {
+                    h = *reinterpret_cast<volatile unsigned long long *>(wq.head);
+                    tl = *reinterpret_cast<volatile unsigned long long *>(wq.tail);
+                }
+                h = __shfl_sync(RT_FULL, h, 0);
+                tl = __shfl_sync(RT_FULL, tl, 0);
+                if (h > tl && (long long)tl < wq.cap) {
+                    const int give = top / 2;
+                    long long pos = 0;
+                    if (lane == 0)
+                        pos = (long long)atomicAdd(wq.tail, (unsigned long long)give);
+                    pos = __shfl_sync(RT_FULL, pos, 0);
+                    const long long room = wq.cap - pos;
+                    const int n = room <= 0 ? 0 : (room < give ? (int)room : give);
+                    if (n > 0) {
+                        if (lane == 0)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(wq.pending),
+                                      (unsigned long long)n);
+                        __threadfence();
+                        for (int e = lane; e < n; e += 32) {
+                            volatile unsigned long long *slot = wq.items + pos + e;
+                            *slot = pack_item((int)qi, st[e]);
+                        }
+                        __syncwarp();
+                        // shift the kept entries down, 32 at a time: a chunk is
+                        // read before it is written, and later chunks read
+                        // strictly higher indices
+                        const int keep = top - n;
+                        for (int c0 = 0; c0 < keep; c0 += 32) {
+                            const int e = c0 + lane;
+                            int v = 0;
+                            if (e < keep)
+                                v = st[n + e];
+                            __syncwarp();
+                            if (e < keep)
+                                st[e] = v;
+                            __syncwarp();
+                        }
+                        top = keep;
+                    }
+                }
+            }
+        }
+        if (stats && lane == 0)
+            flush_stats(stats, wk, root == 0);
+        if (lane == 0) {
+            if (wk.overflow)
+                atomicOr(flags, FLAG_STACK);
+            if (PASS == PASS_COUNT) {
+                if (wk.cur)
+                    atomicAdd(io.counts + qi, (int)wk.cur);
+                if (io.counts_leaf && wk.lcur)
+                    atomicAdd(io.counts_leaf + qi, (int)wk.lcur);
+                if (io.counts_rng && wk.rcur)
+                    atomicAdd(io.counts_rng + qi, (int)wk.rcur);
+            }
+            __threadfence();
+            atomicAdd(reinterpret_cast<unsigned long long *>(wq.pending), ~0ull);  // -1
+        }
+    }
+}
+
+__global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap, int64_t Q)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cap;
+         i += (long long)gridDim.x * blockDim.x)
+        items[i] = i < Q ? pack_item((int)i, 0) : kEmpty;
+}
+
+// After a work-queue scatter/descriptor pass: every query's cursors must
+// have reached its segment length.
+__global__ void k_wq_check(const SelIO io, int pass, int64_t Q, int32_t *__restrict__ flags)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool bad;
+        if (pass == PASS_SCATTER)
+            bad = io.cur_ids[i] != io.offsets[i + 1] - io.offsets[i];
+        else
+            bad = io.cur_leaf[i] != io.off_leaf[i + 1] - io.off_leaf[i] ||
+                  io.cur_rng[i] != io.off_rng[i + 1] - io.off_rng[i];
+        if (bad)
+            atomicOr(flags, FLAG_COUNT_MISMATCH);
     }
 }
 
@@ -279,6 +513,81 @@ rtree_status launch(int pass, const rtree *t, const float4 *q, int64_t Q, const 
     return RTREE_OK;
 }
 
+using WqKernel = void (*)(TreeDev, const float4 *, int64_t, SelIO, WorkQueue, int32_t *, int,
+                          unsigned long long *);
+
+template <int F, int LAYOUT>
+WqKernel pick_wq_pass(int pass)
+{
+    return pass == PASS_COUNT     ? k_select_wq<F, LAYOUT, PASS_COUNT>
+           : pass == PASS_SCATTER ? k_select_wq<F, LAYOUT, PASS_SCATTER>
+                                  : k_select_wq<F, LAYOUT, PASS_DESC>;
+}
+
+template <int F>
+WqKernel pick_wq_layout(int layout, int pass)
+{
+    return layout == RTREE_LAYOUT_AOS ? pick_wq_pass<F, RTREE_LAYOUT_AOS>(pass)
+                                      : pick_wq_pass<F, RTREE_LAYOUT_SOA>(pass);
+}
+
+WqKernel pick_wq(int F, int layout, int pass)
+{
+    switch (F) {
+    case 4: return pick_wq_layout<4>(layout, pass);
+    case 8: return pick_wq_layout<8>(layout, pass);
+    case 16: return pick_wq_layout<16>(layout, pass);
+    case 32: return pick_wq_layout<32>(layout, pass);
+    case 64: return pick_wq_layout<64>(layout, pass);
+    case 128: return pick_wq_layout<128>(layout, pass);
+    default: return nullptr;
+    }
+}
+
+// One pass with the persistent work-queue mapping.  io's per-query outputs
+// (counts for COUNT, cursors otherwise) must be zeroed by the caller.
+rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, const SelIO &io,
+                       int32_t *flags, cudaStream_t s, unsigned long long *stats = nullptr)
+{
+    WqKernel kern = pick_wq(t->fanout, t->layout, pass);
+    if (!kern)
+        return fail(RTREE_EINVAL, "unsupported fanout %d", t->fanout);
+    const int cap = t->levels * (t->fanout > 32 ? t->fanout : 32);
+    const size_t smem = (size_t)kWarps * cap * sizeof(int32_t);
+    if (smem > 48 * 1024)
+        RT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1)
+        return fail(RTREE_EOVERFLOW, "select kernel does not fit on an SM (%zu B shared)", smem);
+    const int64_t grid = (int64_t)per_sm * sm_count();  // persistent: all warps resident
+    const long long cap_items = Q + (Q > (1 << 20) ? Q : (1 << 20));
+    DevBuf<unsigned long long> items(s), ctl(s);
+    RT_TRY(items.alloc(cap_items, "work queue"));
+    RT_TRY(ctl.alloc(3, "work queue counters"));
+    const unsigned long long init[3] = {0ull, (unsigned long long)Q, (unsigned long long)Q};
+    RT_CUDA(cudaMemcpyAsync(ctl.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    {
+        KernelTimer kt_("wq_init", s);
+        int64_t b = (cap_items + 255) / 256;
+        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items.p, cap_items, Q);
+        RT_LAUNCH();
+    }
+    WorkQueue wq{items.p, cap_items, ctl.p, ctl.p + 1, reinterpret_cast<long long *>(ctl.p + 2)};
+    {
+        KernelTimer kt_(pass == PASS_COUNT ? "select_count" : pass == PASS_SCATTER ? "select_scatter" : "select_desc", s);
+        kern<<<(unsigned)grid, kThreads, smem, s>>>(t->view(), q, Q, io, wq, flags, cap, stats);
+        RT_LAUNCH();
+    }
+    if (pass != PASS_COUNT) {
+        KernelTimer kt_("wq_check", s);
+        int64_t b = (Q + 255) / 256;
+        k_wq_check<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(io, pass, Q, flags);
+        RT_LAUNCH();
+    }
+    return RTREE_OK;
+}
+
 rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree_result *res)
 {
     RT_CUDA(cudaMemsetAsync(off.p, 0, (Q + 1) * sizeof(int64_t), s));
@@ -295,7 +604,7 @@ rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
                           int mapping, cudaStream_t s, rtree_result *res)
 {
-    (void)mapping;
+    const bool wq = mapping == RTREE_MAP_WORK_QUEUE;
     res->rows = Q;
     res->total = 0;
     DevBuf<int64_t> off(s);
@@ -308,9 +617,9 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     DevBuf<int32_t> cnt(s), cnt_leaf(s), cnt_rng(s), flags(s);
     DevBuf<unsigned long long> ctr(s);
     RT_TRY(cnt.alloc(Q, "select counts"));
-    RT_TRY(flags.alloc(1, "select flags"));
+    RT_TRY(flags.alloc(2, "select flags"));  // [0] select passes, [1] sort
     RT_TRY(ctr.alloc(2, "select work counters"));
-    RT_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int32_t), s));
+    RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
     RT_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
     SelIO io{};
     io.counts = cnt.p;
@@ -320,7 +629,16 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         io.counts_leaf = cnt_leaf.p;
         io.counts_rng = cnt_rng.p;
     }
-    RT_TRY(launch(PASS_COUNT, t, queries, Q, io, ctr.p, flags.p, s));
+    if (wq) {  // several warps add into one query's counts
+        RT_CUDA(cudaMemsetAsync(cnt.p, 0, Q * sizeof(int32_t), s));
+        if (sorted) {
+            RT_CUDA(cudaMemsetAsync(cnt_leaf.p, 0, Q * sizeof(int32_t), s));
+            RT_CUDA(cudaMemsetAsync(cnt_rng.p, 0, Q * sizeof(int32_t), s));
+        }
+        RT_TRY(launch_wq(PASS_COUNT, t, queries, Q, io, flags.p, s));
+    } else {
+        RT_TRY(launch(PASS_COUNT, t, queries, Q, io, ctr.p, flags.p, s));
+    }
     RT_TRY(scan_exclusive(cnt.p, off.p, Q, s));
     DevBuf<int64_t> off_leaf(s), off_rng(s);
     if (sorted) {
@@ -338,9 +656,16 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     }
     RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RT_CUDA(cudaStreamSynchronize(s));
+    if (hflags & FLAG_TIMEOUT)
+        return fail(RTREE_ETIMEOUT, "select count pass: a work-queue wait exceeded its limit");
     if (hflags)
         return fail(RTREE_EINTERNAL, "select count pass reported device flags 0x%x", hflags);
     const int64_t total = h[0];
+    DevBuf<int32_t> cursors(s);
+    if (wq) {
+        RT_TRY(cursors.alloc(2 * Q, "select cursors"));
+        RT_CUDA(cudaMemsetAsync(cursors.p, 0, 2 * Q * sizeof(int32_t), s));
+    }
 
     DevBuf<int32_t> ids(s);
     RT_TRY(ids.alloc(total, "select ids"));
@@ -348,7 +673,12 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         SelIO so{};
         so.offsets = off.p;
         so.out = ids.p;
-        RT_TRY(launch(PASS_SCATTER, t, queries, Q, so, ctr.p + 1, flags.p, s));
+        if (wq) {
+            so.cur_ids = cursors.p;
+            RT_TRY(launch_wq(PASS_SCATTER, t, queries, Q, so, flags.p, s));
+        } else {
+            RT_TRY(launch(PASS_SCATTER, t, queries, Q, so, ctr.p + 1, flags.p, s));
+        }
     } else {
         DevBuf<int32_t> leaf(s);
         DevBuf<int2> rng(s);
@@ -359,17 +689,29 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         so.off_rng = off_rng.p;
         so.leaf_out = leaf.p;
         so.rng_out = rng.p;
-        RT_TRY(launch(PASS_DESC, t, queries, Q, so, ctr.p + 1, flags.p, s));
+        if (wq) {
+            so.cur_leaf = cursors.p;
+            so.cur_rng = cursors.p + Q;
+            RT_TRY(launch_wq(PASS_DESC, t, queries, Q, so, flags.p, s));
+        } else {
+            RT_TRY(launch(PASS_DESC, t, queries, Q, so, ctr.p + 1, flags.p, s));
+        }
         SortSources src{};
         src.leaf = leaf.p;
         src.off_leaf = off_leaf.p;
         src.rng = rng.p;
         src.off_rng = off_rng.p;
         src.tree_ids = t->ids;
-        RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s));
+        RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s, flags.p + 1));
     }
-    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    int32_t hf2[2] = {0, 0};
+    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
     RT_CUDA(cudaStreamSynchronize(s));
+    if (hf2[1])
+        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
+    hflags = hf2[0];
+    if (hflags & FLAG_TIMEOUT)
+        return fail(RTREE_ETIMEOUT, "select second pass: a work-queue wait exceeded its limit");
     if (hflags)
         return fail(RTREE_EINTERNAL, "select scatter pass reported device flags 0x%x", hflags);
     res->total = total;

@@ -202,3 +202,31 @@ def test_crowded_buckets_fall_back_to_lsd(rt):
     assert ((counts > 256) & (counts <= 16384)).sum() > 20
     got = select_gpu(rt, rects, ids, queries, fanout=16)
     assert_csr_equal(got, want, "crowded buckets")
+
+
+@pytest.mark.parametrize("unsorted", [False, True])
+def test_work_queue_mapping(rt, unsorted):
+    """The persistent work-queue mapping (warps split large queries between
+    them) gives the same result sets as the oracle; heavy queries included."""
+    w = dg.workload("uneven", n=400_000, q=6000)
+    want = oracle.Tree(w.rects, w.ids, 16).select(w.queries)
+    for F, layout in ((16, "soa"), (64, "aos"), (4, "soa")):
+        off, ids = select_gpu(rt, w.rects, w.ids, w.queries, fanout=F, layout=layout,
+                              mapping="work_queue", unsorted=unsorted)
+        assert np.array_equal(off, want[0]), (F, layout)
+        if unsorted:
+            for i in range(len(off) - 1):
+                seg = np.sort(ids[off[i]:off[i + 1]])
+                assert np.array_equal(seg, want[1][off[i]:off[i + 1]]), (F, i)
+        else:
+            assert np.array_equal(ids, want[1]), (F, layout)
+
+
+def test_work_queue_mapping_small_and_empty(rt):
+    for n, q in ((1, 5), (17, 40), (3000, 1)):
+        rects = random_case("grid", n, n)
+        queries = np.concatenate([random_case("grid", q, n + 3),
+                                  np.array([[-INF, -INF, INF, INF]], np.float32)])
+        want = oracle.Tree(rects, None, 8).select(queries)
+        got = select_gpu(rt, rects, None, queries, fanout=8, mapping="work_queue")
+        assert_csr_equal(got, want, f"wq n={n}")
