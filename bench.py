@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fanout", type=int, default=0, help="0: pick by timing 16/32/64")
     ap.add_argument("--layout", choices=["soa", "aos", "auto"], default="auto")
+    ap.add_argument("--mapping", choices=["warp_per_query", "work_queue", "auto"], default="auto")
     ap.add_argument("--n", type=int, default=None, help="override rectangles (testing only)")
     ap.add_argument("--q", type=int, default=None, help="override queries (testing only)")
     ap.add_argument("--sel", type=float, nargs=2, default=None, metavar=("LO", "HI"),
@@ -55,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-join", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
     return ap.parse_args()
 
 
@@ -239,9 +241,9 @@ def run_ours(args):
     queries = torch.from_numpy(w.queries).to(dev)
     torch.cuda.synchronize()
 
-    def step(F, layout):
+    def step(F, layout, mapping):
         t = rt.RTree(rects, ids, fanout=F, layout=layout, stream=stream)
-        res = t.range_select(queries, stream=stream)
+        res = t.range_select(queries, mapping=mapping, stream=stream)
         total = res.total
         res.close()
         t.close()
@@ -250,22 +252,25 @@ def run_ours(args):
     # ---- pick fanout/layout by timing one step each (untimed for the result)
     fanouts = [args.fanout] if args.fanout else [16, 32, 64]
     layouts = ["soa", "aos"] if args.layout == "auto" else [args.layout]
+    mappings = ["warp_per_query", "work_queue"] if args.mapping == "auto" else [args.mapping]
     sweep = {}
     total_hits = None
+    step(fanouts[0], layouts[0], mappings[0])  # first touch / pool growth
     for F in fanouts:
         for lay in layouts:
-            step(F, lay)  # first touch / pool growth
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            total_hits = step(F, lay)
-            torch.cuda.synchronize()
-            sweep[f"F{F}_{lay}"] = round((time.perf_counter() - t0) * 1e3, 3)
+            for mp in mappings:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                total_hits = step(F, lay, mp)
+                torch.cuda.synchronize()
+                sweep[f"F{F}_{lay}_{mp}"] = round((time.perf_counter() - t0) * 1e3, 3)
     best = min(sweep, key=sweep.get)
     F = int(best.split("_")[0][1:])
     layout = best.split("_")[1]
+    mapping = best.split("_", 2)[2]
 
     for _ in range(args.warmup):
-        step(F, layout)
+        step(F, layout, mapping)
     torch.cuda.synchronize()
 
     # ---- timed region
@@ -280,7 +285,7 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(F, layout)
+        step(F, layout, mapping)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -336,7 +341,7 @@ def run_ours(args):
 
         def e2e_step():
             h = rt.rtree_build(h_rects, h_ids, F, layout, stream)
-            r = rt.rtree_range_select(h, h_q, stream=stream)
+            r = rt.rtree_range_select(h, h_q, mapping=mapping, stream=stream)
             rc = lib.rtree_result_copy_to_host(r, h_off.data_ptr(), h_out.data_ptr(), sptr)
             assert rc == 0, rt.rtree_last_error()
             rt.rtree_result_free(r)
@@ -353,6 +358,11 @@ def run_ours(args):
         e2e = {"value": round(Q * k2 * world / el, 1), "unit": UNIT,
                "h2d_bytes_per_step": int(w.rects.nbytes + w.ids.nbytes + w.queries.nbytes),
                "d2h_bytes_per_step": int(8 * (Q + 1) + 4 * int(total_hits)), "steps": k2}
+
+    # ---- batched uneven select: graph-captured plans vs one query per launch
+    uneven = None
+    if not args.no_uneven:
+        uneven = run_uneven(args, rt, dg, torch, dev, stream, rank, world, F, layout)
 
     # ---- join workload (R, S 2M each, fanout 32)
     join = None
@@ -399,7 +409,8 @@ def run_ours(args):
             "config": {"workload": f"scaled range select: {N} rects (80% 64-cluster gaussian, "
                                    f"20% uniform, sides log-U[1e-5,1e-3]), {Q} queries "
                                    "(selectivity log-U[1e-6,1e-3]), STR build + sorted select per step",
-                       "fanout": F, "layout": layout, "ids_returned_per_step": int(total_hits),
+                       "fanout": F, "layout": layout, "mapping": mapping,
+                       "ids_returned_per_step": int(total_hits),
                        "l2": "inputs larger than L2 (rects 160 MB, tree ~200 MB; no flush)",
                        "sweep_ms_per_step": sweep, "seed": seed},
             "gpu_launches": int(launches),
@@ -409,12 +420,72 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "join": join,
+            "uneven": uneven,
             "select_stats": stats,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_uneven(args, rt, dg, torch, dev, stream, rank, world, F, layout):
+    """The heavy-tailed batch (10M-rect index, 100k queries, 1% large): the
+    graph-captured batched form against one query per launch."""
+    u = dg.workload("uneven", seed=3 + 1000 * rank, n=args.n, q=None if args.q is None else args.q // 10)
+    Q = u.queries.shape[0]
+    q_dev = torch.from_numpy(u.queries).to(dev)
+    tree = rt.RTree(torch.from_numpy(u.rects).to(dev), torch.from_numpy(u.ids).to(dev), fanout=F,
+                    layout=layout, stream=stream)
+    res = tree.range_select(q_dev, stream=stream)
+    total = res.total
+    res.close()
+    reps = max(3, args.steps)
+    out = {"workload": f"uneven: {u.rects.shape[0]} rects, {Q} queries per batch (1% with sides "
+                       "U[0.05,0.2]), sorted results", "fanout": F, "layout": layout,
+           "ids_per_batch": int(total)}
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for mapping in ("warp_per_query", "work_queue"):
+        plan = rt.Plan(tree, Q, int(total * 1.02) + 4096, mapping)
+        ms = timed(lambda: plan.run(q_dev, stream), reps)
+        out[f"graph_{mapping}_qps"] = round(Q * world / (ms / 1e3), 1)
+        out[f"graph_{mapping}_ms"] = round(ms, 3)
+        plan.close()
+
+    def plain(mapping):
+        r = tree.range_select(q_dev, mapping=mapping, stream=stream)
+        r.close()
+
+    for mapping in ("warp_per_query", "work_queue"):
+        ms = timed(lambda: plain(mapping), reps)
+        out[f"call_{mapping}_qps"] = round(Q * world / (ms / 1e3), 1)
+    # one query per launch: every query its own select call (sample of 2000)
+    sample = q_dev[:2000]
+    n1 = sample.shape[0]
+
+    def one_by_one():
+        for i in range(n1):
+            r = tree.range_select(sample[i:i + 1], stream=stream)
+            r.close()
+
+    ms = timed(one_by_one, 1)
+    out["one_query_per_launch_qps"] = round(n1 * world / (ms / 1e3), 1)
+    best = max(v for k, v in out.items() if k.startswith("graph_") and k.endswith("_qps"))
+    out["batched_over_one_per_launch"] = round(best / out["one_query_per_launch_qps"], 1)
+    tree.close()
+    return out
 
 
 # ------------------------------------------------------------- reference

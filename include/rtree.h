@@ -169,6 +169,38 @@ RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *quer
                                 rtree_result_t **out);
 
 /*
+ * Plans: batched range select captured in CUDA graphs (the persistent
+ * batched form of the select).
+ *
+ * A plan owns every device buffer a sorted select needs, sized for at most
+ * max_queries queries and max_ids result ids per batch, and records the whole
+ * device pipeline of rtree_range_select (count pass, scans, descriptor pass,
+ * segmented sort, copy of the totals) as one CUDA graph per batch-size bucket
+ * (powers of two from 256 up to max_queries); a batch is padded to its bucket
+ * with NaN queries, which match nothing.  Unlike rtree_range_select, a run
+ * needs no host round trip between kernels, so small batches cost one graph
+ * launch.  opts->mapping selects warp-per-query or the work queue; plans
+ * always sort.  The tree must outlive the plan.
+ *
+ * rtree_plan_run copies q <= max_queries queries (host or device) into the
+ * plan, runs the batch on `stream` and returns when it has finished; *total
+ * receives the number of ids.  The results are rtree_plan_offsets (device
+ * int64[q+1]) and rtree_plan_ids (device int32[total]), valid until the next
+ * run.  If the batch needs more than max_ids ids, the run returns
+ * RTREE_EOVERFLOW with *total set to the size needed and incomplete outputs.
+ * The first run of each bucket records its graph (it must not itself be
+ * inside a stream capture).  A plan is used by one host thread at a time.
+ */
+typedef struct rtree_plan rtree_plan_t;
+RTREE_API rtree_status rtree_plan_create(const rtree_t *tree, int64_t max_queries, int64_t max_ids,
+                                         const rtree_select_opts_t *opts, rtree_plan_t **out);
+RTREE_API rtree_status rtree_plan_run(rtree_plan_t *plan, const float *queries, int64_t q,
+                                      void *stream, int64_t *total);
+RTREE_API const int64_t *rtree_plan_offsets(const rtree_plan_t *plan);
+RTREE_API const int32_t *rtree_plan_ids(const rtree_plan_t *plan);
+RTREE_API void rtree_plan_free(rtree_plan_t *plan);
+
+/*
  * rtree_range_select_noalloc -- range select that allocates no device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

@@ -87,6 +87,11 @@ class KernelTimer {
 };
 // Resolves recorded event pairs into totals (call after a stream sync).
 void timing_resolve();
+// Graph capture on this thread: launches are counted, not timed; each replay
+// of the captured graph adds its launch count under `name`.
+void timing_capture_begin();
+long long timing_capture_end();
+void timing_add_replay(const char *name, long long launches);
 
 // -------------------------------------------------------------------- tree
 // Device view of a tree.  Nodes of all levels are numbered level by level
@@ -227,7 +232,40 @@ struct SelIO {
     int32_t *cur_ids;         // SCATTER
     int32_t *cur_leaf;        // DESC
     int32_t *cur_rng;         // DESC
+    // Buffer capacities (entries); writes at or past them are dropped.  Only
+    // the graph-captured plan sizes buffers before knowing the totals.
+    int64_t out_cap;
+    int64_t leaf_cap;
+    int64_t rng_cap;
 };
+
+// Caller-owned buffers for a select enqueued without host synchronization
+// (q = number of queries): per-query counts [q], offsets [q+1], the leaf-hit,
+// range and id outputs with their capacities, work-queue cursors [2q],
+// flags [2] (select, sort) and work counters [2].  After the stream finishes,
+// off[q], off_leaf[q] and off_rng[q] hold the totals; a total above its
+// capacity means the outputs are incomplete.
+struct SelectBuffers {
+    int32_t *cnt, *cnt_leaf, *cnt_rng;
+    int64_t *off, *off_leaf, *off_rng;
+    int32_t *leaf;
+    int64_t leaf_cap;
+    int2 *rng;
+    int64_t rng_cap;
+    int32_t *ids;
+    int64_t ids_cap;
+    int32_t *cursors;
+    int32_t *flags;
+    unsigned long long *ctr;
+    unsigned long long *wq_ctl;  // 3 words, work-queue mapping
+    unsigned long long *wq_items;
+    long long wq_cap;
+};
+
+// Enqueues a sorted range select into `b` on stream s (capturable in a CUDA
+// graph: no host synchronization, no pageable copies).
+rtree_status select_enqueue(const rtree *t, const float4 *queries, int64_t q, int mapping,
+                            const SelectBuffers &b, cudaStream_t s);
 
 // Where the ids of segment i come from: leaf[off_leaf[i] .. off_leaf[i+1])
 // followed by tree_ids[lo .. hi) for every (lo, hi) in
@@ -238,6 +276,8 @@ struct SortSources {
     const int2 *rng;
     const int64_t *off_rng;
     const int32_t *tree_ids;
+    int64_t leaf_cap;  // 0: unchecked; else segments reaching past are skipped
+    int64_t rng_cap;
 };
 
 // Writes segment i's ids, sorted ascending (signed), to

@@ -68,7 +68,7 @@ __device__ __forceinline__ int class_of(int64_t n)
 __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_t *__restrict__ lists,
                            int64_t stride, int64_t *__restrict__ large_tmp,
                            unsigned long long *__restrict__ hdr, SortSources S,
-                           int32_t *__restrict__ out)
+                           int32_t *__restrict__ out, int64_t out_cap)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -76,7 +76,13 @@ __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = warp * 32; b < nseg; b += nwarps * 32) {
         const int64_t i = b + lane;
-        const int64_t len = i < nseg ? off[i + 1] - off[i] : 0;
+        int64_t len = i < nseg ? off[i + 1] - off[i] : 0;
+        // a segment whose output or sources reach past a buffer's capacity is
+        // skipped (the caller sees the totals exceed the capacities)
+        if (len > 0 && (off[i + 1] > out_cap ||
+                        (S.leaf_cap && S.off_leaf[i + 1] > S.leaf_cap) ||
+                        (S.rng && S.rng_cap && S.off_rng[i + 1] > S.rng_cap)))
+            len = 0;
         const int cls = class_of(len);
         if (len == 1) {  // a single id: copy it from its source
             int32_t v;
@@ -988,7 +994,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
             blocks = (int64_t)sms * 16;
         KernelTimer kt_("sort_classify", s);
         k_classify<<<(unsigned)blocks, 256, 0, s>>>(offsets, nseg, lists.p, nseg, large_tmp.p, hdr.p,
-                                                    S, out);
+                                                    S, out, total);
         RT_LAUNCH();
     }
     auto L = [&](int c) { return lists.p + (int64_t)c * nseg; };

@@ -132,13 +132,13 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         if (PASS == PASS_SCATTER && me) {
             const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, __popc(me), lane) : sg.base + wk.cur;
             const int64_t o = at + __popc(me & lt);
-            if (emit && o < sg.lim)
+            if (emit && o < sg.lim && o < io.out_cap)
                 io.out[o] = __ldg(t.ids + m.x + j);
         }
         if (PASS == PASS_DESC && me) {
             const int64_t at = WQ ? sg.lbase + reserve(io.cur_leaf + qi, __popc(me), lane) : sg.lbase + wk.lcur;
             const int64_t o = at + __popc(me & lt);
-            if (emit && o < sg.llim)
+            if (emit && o < sg.llim && o < io.leaf_cap)
                 io.leaf_out[o] = __ldg(t.ids + m.x + j);
         }
         wk.cur += __popc(me);
@@ -154,7 +154,7 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
             if (PASS == PASS_DESC) {
                 const int64_t at = WQ ? sg.rbase + reserve(io.cur_rng + qi, __popc(mc), lane) : sg.rbase + wk.rcur;
                 const int64_t o = at + __popc(mc & lt);
-                if (cont && o < sg.rlim)
+                if (cont && o < sg.rlim && o < io.rng_cap)
                     io.rng_out[o] = make_int2(lo, hi);
             }
             wk.rcur += __popc(mc);
@@ -166,7 +166,8 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
                     const int l = __shfl_sync(RT_FULL, lo, src);
                     const int h = __shfl_sync(RT_FULL, hi, src);
                     const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, h - l, lane) : sg.base + wk.cur;
-                    const int64_t room = sg.lim - at;
+                    const int64_t end = sg.lim < io.out_cap ? sg.lim : io.out_cap;
+                    const int64_t room = end - at;
                     const int hh = (int64_t)(h - l) <= room ? h : l + (int)(room > 0 ? room : 0);
                     warp_copy(io.out + at, t.ids, l, hh, lane);
                     wk.cur += h - l;
@@ -428,11 +429,17 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-__global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap, int64_t Q)
+__global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap, int64_t Q,
+                          unsigned long long *__restrict__ ctl)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cap;
          i += (long long)gridDim.x * blockDim.x)
         items[i] = i < Q ? pack_item((int)i, 0) : kEmpty;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl[0] = 0;                        // head
+        ctl[1] = (unsigned long long)Q;    // tail
+        ctl[2] = (unsigned long long)Q;    // pending
+    }
 }
 
 // After a work-queue scatter/descriptor pass: every query's cursors must
@@ -547,7 +554,9 @@ WqKernel pick_wq(int F, int layout, int pass)
 // One pass with the persistent work-queue mapping.  io's per-query outputs
 // (counts for COUNT, cursors otherwise) must be zeroed by the caller.
 rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, const SelIO &io,
-                       int32_t *flags, cudaStream_t s, unsigned long long *stats = nullptr)
+                       int32_t *flags, cudaStream_t s, unsigned long long *stats = nullptr,
+                       unsigned long long *ext_items = nullptr, long long ext_cap = 0,
+                       unsigned long long *ext_ctl = nullptr)
 {
     WqKernel kern = pick_wq(t->fanout, t->layout, pass);
     if (!kern)
@@ -561,19 +570,23 @@ rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, con
     if (per_sm < 1)
         return fail(RTREE_EOVERFLOW, "select kernel does not fit on an SM (%zu B shared)", smem);
     const int64_t grid = (int64_t)per_sm * sm_count();  // persistent: all warps resident
-    const long long cap_items = Q + (Q > (1 << 20) ? Q : (1 << 20));
+    long long cap_items = ext_cap;
     DevBuf<unsigned long long> items(s), ctl(s);
-    RT_TRY(items.alloc(cap_items, "work queue"));
-    RT_TRY(ctl.alloc(3, "work queue counters"));
-    const unsigned long long init[3] = {0ull, (unsigned long long)Q, (unsigned long long)Q};
-    RT_CUDA(cudaMemcpyAsync(ctl.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    unsigned long long *items_p = ext_items, *ctl_p = ext_ctl;
+    if (!items_p) {
+        cap_items = Q + (Q > (1 << 20) ? Q : (1 << 20));
+        RT_TRY(items.alloc(cap_items, "work queue"));
+        RT_TRY(ctl.alloc(3, "work queue counters"));
+        items_p = items.p;
+        ctl_p = ctl.p;
+    }
     {
         KernelTimer kt_("wq_init", s);
         int64_t b = (cap_items + 255) / 256;
-        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items.p, cap_items, Q);
+        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items_p, cap_items, Q, ctl_p);
         RT_LAUNCH();
     }
-    WorkQueue wq{items.p, cap_items, ctl.p, ctl.p + 1, reinterpret_cast<long long *>(ctl.p + 2)};
+    WorkQueue wq{items_p, cap_items, ctl_p, ctl_p + 1, reinterpret_cast<long long *>(ctl_p + 2)};
     {
         KernelTimer kt_(pass == PASS_COUNT ? "select_count" : pass == PASS_SCATTER ? "select_scatter" : "select_desc", s);
         kern<<<(unsigned)grid, kThreads, smem, s>>>(t->view(), q, Q, io, wq, flags, cap, stats);
@@ -586,6 +599,13 @@ rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, con
         RT_LAUNCH();
     }
     return RTREE_OK;
+}
+
+SelIO unlimited()
+{
+    SelIO io{};
+    io.out_cap = io.leaf_cap = io.rng_cap = INT64_MAX;
+    return io;
 }
 
 rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree_result *res)
@@ -621,7 +641,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     RT_TRY(ctr.alloc(2, "select work counters"));
     RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
     RT_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
-    SelIO io{};
+    SelIO io = unlimited();
     io.counts = cnt.p;
     if (sorted) {
         RT_TRY(cnt_leaf.alloc(Q, "select counts"));
@@ -670,7 +690,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     DevBuf<int32_t> ids(s);
     RT_TRY(ids.alloc(total, "select ids"));
     if (!sorted) {
-        SelIO so{};
+        SelIO so = unlimited();
         so.offsets = off.p;
         so.out = ids.p;
         if (wq) {
@@ -684,7 +704,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         DevBuf<int2> rng(s);
         RT_TRY(leaf.alloc(h[1], "select leaf hits"));
         RT_TRY(rng.alloc(h[2], "select whole subtrees"));
-        SelIO so{};
+        SelIO so = unlimited();
         so.off_leaf = off_leaf.p;
         so.off_rng = off_rng.p;
         so.leaf_out = leaf.p;
@@ -720,11 +740,66 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     return RTREE_OK;
 }
 
+rtree_status select_enqueue(const rtree *t, const float4 *queries, int64_t Q, int mapping,
+                            const SelectBuffers &b, cudaStream_t s)
+{
+    const bool wq = mapping == RTREE_MAP_WORK_QUEUE;
+    RT_CUDA(cudaMemsetAsync(b.flags, 0, 2 * sizeof(int32_t), s));
+    RT_CUDA(cudaMemsetAsync(b.ctr, 0, 2 * sizeof(unsigned long long), s));
+    if (Q == 0 || t->nodes == 0) {
+        RT_CUDA(cudaMemsetAsync(b.off, 0, (Q + 1) * sizeof(int64_t), s));
+        RT_CUDA(cudaMemsetAsync(b.off_leaf, 0, (Q + 1) * sizeof(int64_t), s));
+        RT_CUDA(cudaMemsetAsync(b.off_rng, 0, (Q + 1) * sizeof(int64_t), s));
+        return RTREE_OK;
+    }
+    SelIO io = unlimited();
+    io.counts = b.cnt;
+    io.counts_leaf = b.cnt_leaf;
+    io.counts_rng = b.cnt_rng;
+    if (wq) {
+        RT_CUDA(cudaMemsetAsync(b.cnt, 0, Q * sizeof(int32_t), s));
+        RT_CUDA(cudaMemsetAsync(b.cnt_leaf, 0, Q * sizeof(int32_t), s));
+        RT_CUDA(cudaMemsetAsync(b.cnt_rng, 0, Q * sizeof(int32_t), s));
+        RT_TRY(launch_wq(PASS_COUNT, t, queries, Q, io, b.flags, s, nullptr, b.wq_items, b.wq_cap,
+                         b.wq_ctl));
+    } else {
+        RT_TRY(launch(PASS_COUNT, t, queries, Q, io, b.ctr, b.flags, s));
+    }
+    RT_TRY(scan_exclusive(b.cnt, b.off, Q, s));
+    RT_TRY(scan_exclusive(b.cnt_leaf, b.off_leaf, Q, s));
+    RT_TRY(scan_exclusive(b.cnt_rng, b.off_rng, Q, s));
+    SelIO so = unlimited();
+    so.off_leaf = b.off_leaf;
+    so.off_rng = b.off_rng;
+    so.leaf_out = b.leaf;
+    so.rng_out = b.rng;
+    so.leaf_cap = b.leaf_cap;
+    so.rng_cap = b.rng_cap;
+    if (wq) {
+        RT_CUDA(cudaMemsetAsync(b.cursors, 0, 2 * Q * sizeof(int32_t), s));
+        so.cur_leaf = b.cursors;
+        so.cur_rng = b.cursors + Q;
+        RT_TRY(launch_wq(PASS_DESC, t, queries, Q, so, b.flags, s, nullptr, b.wq_items, b.wq_cap,
+                         b.wq_ctl));
+    } else {
+        RT_TRY(launch(PASS_DESC, t, queries, Q, so, b.ctr + 1, b.flags, s));
+    }
+    SortSources src{};
+    src.leaf = b.leaf;
+    src.off_leaf = b.off_leaf;
+    src.rng = b.rng;
+    src.off_rng = b.off_rng;
+    src.tree_ids = t->ids;
+    src.leaf_cap = b.leaf_cap;
+    src.rng_cap = b.rng_cap;
+    return segmented_sort_gather(b.ids, b.off, Q, b.ids_cap, src, s, b.flags + 1);
+}
+
 rtree_status select_pass(const rtree *t, const float4 *queries, int64_t Q, int32_t *counts,
                          const int64_t *offsets, int32_t *out, unsigned long long *ctr,
                          int32_t *flags, cudaStream_t s)
 {
-    SelIO io{};
+    SelIO io = unlimited();
     io.counts = counts;
     io.offsets = offsets;
     io.out = out;
@@ -748,7 +823,7 @@ rtree_status select_stats(const rtree *t, const float4 *queries, int64_t Q, cuda
     RT_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int32_t), s));
     RT_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long), s));
     RT_CUDA(cudaMemsetAsync(st.p, 0, 8 * sizeof(unsigned long long), s));
-    SelIO io{};
+    SelIO io = unlimited();
     io.counts = cnt.p;
     RT_TRY(launch(PASS_COUNT, t, queries, Q, io, ctr.p, flags.p, s, st.p));
     unsigned long long h[8];

@@ -73,8 +73,33 @@ void resolve_locked()
 
 }  // namespace
 
+// While this thread captures a CUDA graph, launches are counted here (the
+// graph's replays add them later) and no events are recorded.
+thread_local long long t_capture_launches = -1;
+
+void timing_capture_begin() { t_capture_launches = 0; }
+
+long long timing_capture_end()
+{
+    const long long n = t_capture_launches;
+    t_capture_launches = -1;
+    return n < 0 ? 0 : n;
+}
+
+void timing_add_replay(const char *name, long long launches)
+{
+    std::lock_guard<std::mutex> g(g_mu);
+    const int e = entry_for(name);
+    g_entries[e].launches += launches;
+    g_total_launches += launches;
+}
+
 KernelTimer::KernelTimer(const char *name, cudaStream_t s) : s_(s)
 {
+    if (t_capture_launches >= 0) {
+        ++t_capture_launches;
+        return;
+    }
     std::lock_guard<std::mutex> g(g_mu);
     entry_ = entry_for(name);
     g_entries[entry_].launches++;

@@ -74,6 +74,11 @@ def _bind(lib):
         "rtree_last_error": (C.c_char_p, []),
         "rtree_version": (C.c_char_p, []),
         "rtree_debug_fail_alloc_after": (None, [C.c_longlong]),
+        "rtree_plan_create": (C.c_int, [vp, i64, i64, C.POINTER(rtree_select_opts_t), C.POINTER(vp)]),
+        "rtree_plan_run": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
+        "rtree_plan_offsets": (vp, [vp]),
+        "rtree_plan_ids": (vp, [vp]),
+        "rtree_plan_free": (None, [vp]),
         "rtree_timing_enable": (None, [C.c_int]),
         "rtree_timing_reset": (None, []),
         "rtree_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
@@ -299,6 +304,40 @@ def rtree_debug_fail_alloc_after(k: int) -> None:
     load_library().rtree_debug_fail_alloc_after(int(k))
 
 
+def rtree_plan_create(handle: int, max_queries: int, max_ids: int, mapping: str | int = "auto") -> int:
+    """Creates a graph-captured batched select plan (see the C header)."""
+    lib = load_library()
+    opts = rtree_select_opts_t()
+    opts.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
+    out = C.c_void_p()
+    _check(lib.rtree_plan_create(handle, int(max_queries), int(max_ids), C.byref(opts), C.byref(out)), lib)
+    return out.value
+
+
+def rtree_plan_run(plan: int, queries, stream=None) -> int:
+    """Runs one batch; returns the number of ids (results stay in the plan)."""
+    lib = load_library()
+    qp, q, keep = _as_rows(queries, "queries")
+    total = C.c_int64()
+    rc = lib.rtree_plan_run(plan, qp, q, _stream(stream), C.byref(total))
+    del keep
+    _check(rc, lib)
+    return total.value
+
+
+def rtree_plan_offsets(plan: int) -> int:
+    return load_library().rtree_plan_offsets(plan) or 0
+
+
+def rtree_plan_ids(plan: int) -> int:
+    return load_library().rtree_plan_ids(plan) or 0
+
+
+def rtree_plan_free(plan: int) -> None:
+    if plan:
+        load_library().rtree_plan_free(plan)
+
+
 def rtree_timing_enable(on: bool = True) -> None:
     load_library().rtree_timing_enable(1 if on else 0)
 
@@ -376,6 +415,45 @@ class Result:
         if self.total == 0:
             return torch.zeros(shape, dtype=torch.int32, device="cuda")
         return torch.as_tensor(_DeviceArray(self, ptr, shape, "<i4"), device="cuda")
+
+
+class Plan:
+    """A graph-captured batched select over one tree (keeps the tree alive)."""
+
+    def __init__(self, tree: "RTree", max_queries: int, max_ids: int, mapping="auto"):
+        self.tree = tree
+        self.handle = None
+        self.handle = rtree_plan_create(tree.handle, max_queries, max_ids, mapping)
+        self.q = 0
+        self.total = 0
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            rtree_plan_free(h)
+
+    def run(self, queries, stream=None) -> int:
+        self.q = int(queries.shape[0])
+        self.total = rtree_plan_run(self.handle, queries, stream)
+        return self.total
+
+    def offsets_tensor(self):
+        import torch
+        ptr = rtree_plan_offsets(self.handle)
+        return torch.as_tensor(_DeviceArray(self, ptr, (self.q + 1,), "<i8"), device="cuda")
+
+    def ids_tensor(self):
+        import torch
+        if self.total == 0:
+            return torch.zeros(0, dtype=torch.int32, device="cuda")
+        ptr = rtree_plan_ids(self.handle)
+        return torch.as_tensor(_DeviceArray(self, ptr, (self.total,), "<i4"), device="cuda")
+
+    def to_numpy(self):
+        return self.offsets_tensor().cpu().numpy(), self.ids_tensor().cpu().numpy()
 
 
 class RTree:
