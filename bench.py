@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-join", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-n", type=int, default=50_000_000, help="index size of the serving run")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -364,6 +367,11 @@ def run_ours(args):
     if not args.no_uneven:
         uneven = run_uneven(args, rt, dg, torch, dev, stream, rank, world, F, layout)
 
+    # ---- serving loop: Poisson request stream over a resident index
+    serve = None
+    if not args.no_serve:
+        serve = run_serve(args, rt, dg, torch, dev, rank, world, F, layout)
+
     # ---- join workload (R, S 2M each, fanout 32)
     join = None
     if not args.no_join:
@@ -421,6 +429,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "join": join,
             "uneven": uneven,
+            "serve": serve,
             "select_stats": stats,
         }
         print(json.dumps(line), flush=True)
@@ -484,6 +493,72 @@ def run_uneven(args, rt, dg, torch, dev, stream, rank, world, F, layout):
     out["one_query_per_launch_qps"] = round(n1 * world / (ms / 1e3), 1)
     best = max(v for k, v in out.items() if k.startswith("graph_") and k.endswith("_qps"))
     out["batched_over_one_per_launch"] = round(best / out["one_query_per_launch_qps"], 1)
+    tree.close()
+    return out
+
+
+def run_serve(args, rt, dg, torch, dev, rank, world, F, layout):
+    """A Poisson stream of requests over a resident index: 90% single range
+    queries (selectivity log-uniform in [1e-7, 1e-3]), 10% probe joins of 1k-10k
+    uniform rectangles.  One client thread submits at the arrival times,
+    another collects the replies; the server batches continuously."""
+    import threading
+    w = dg.workload("serve", seed=4 + 1000 * rank, n=args.serve_n, q=1)
+    tree = rt.RTree(torch.from_numpy(w.rects).to(dev), torch.from_numpy(w.ids).to(dev), fanout=F,
+                    layout=layout)
+    del w
+    rng = dg.rng_for(40 + rank)
+    n_req = args.serve_requests
+    mean_side = dg._log_uniform_mean(1e-5, 1e-3)
+    kinds = rng.random(n_req) < 0.10
+    reqs = []
+    for k in range(n_req):
+        if kinds[k]:
+            m = 1000 + int(rng.random() * 9000)
+            reqs.append((rt.RTREE_REQ_PROBE_JOIN, dg.uniform_rects(m, rng, 0.0, 1e-3)))
+        else:
+            reqs.append((rt.RTREE_REQ_SELECT, dg.selectivity_queries(1, rng, 1e-7, 1e-3, mean_side)))
+    n_queries = sum(r[1].shape[0] for r in reqs)
+    out = {"workload": f"serving: {tree.info()['n']} rects (50/50 uniform/clustered), {n_req} requests "
+                       "(90% single range queries, selectivity log-U[1e-7,1e-3]; 10% probe joins of "
+                       "1k-10k uniform rects), Poisson arrivals", "queries_per_run": int(n_queries),
+           "runs": []}
+    srv = rt.Server(tree, workers=3, max_batch_queries=65536, max_batch_ids=64 << 20)
+    # warm: capture the graphs of the common batch sizes
+    warm = [srv.submit(r[1], r[0]) for r in reqs[:200]]
+    for tk in warm:
+        srv.wait(tk)
+    for rate in (5000.0, 20000.0, 80000.0):
+        srv.reset_stats()
+        gaps = -np.log(1.0 - rng.random(n_req)) / rate
+        arrivals = np.cumsum(gaps)
+        tickets = [None] * n_req
+        got = [0]
+
+        def collect():
+            for i in range(n_req):
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                srv.wait(tickets[i])
+                got[0] += 1
+
+        col = threading.Thread(target=collect)
+        col.start()
+        t0 = time.perf_counter()
+        for i, (kind, rects) in enumerate(reqs):
+            while time.perf_counter() - t0 < arrivals[i]:
+                pass
+            tickets[i] = srv.submit(rects, kind)
+        col.join()
+        el = time.perf_counter() - t0
+        st = srv.stats()
+        out["runs"].append({
+            "offered_req_s": rate, "achieved_req_s": round(n_req / el, 1),
+            "queries_s": round(n_queries / el, 1), "p50_ms": round(st["p50_us"] / 1e3, 3),
+            "p99_ms": round(st["p99_us"] / 1e3, 3), "max_ms": round(st["max_us"] / 1e3, 3),
+            "batches": st["batches"], "mean_batch_queries": round(st["batch_queries"] / max(1, st["batches"]), 1),
+            "splits": st["splits"], "fallbacks": st["fallbacks"]})
+    srv.stop()
     tree.close()
     return out
 

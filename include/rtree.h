@@ -201,6 +201,76 @@ RTREE_API const int32_t *rtree_plan_ids(const rtree_plan_t *plan);
 RTREE_API void rtree_plan_free(rtree_plan_t *plan);
 
 /*
+ * Serving: a request loop over a device-resident index with continuous
+ * batching.
+ *
+ * rtree_server_start launches `workers` host threads, each with its own CUDA
+ * stream and plan (max_batch_queries queries, max_batch_ids ids), so several
+ * batches run on the device at once.  Requests wait in a queue; a free worker
+ * takes the waiting requests in arrival order while the batch's queries fit
+ * its plan and their expected result (a running mean of ids per query) fits
+ * 80% of the plan's id capacity -- admission by output memory.  A batch that
+ * still overflows is split in two and rerun; a single request too large for
+ * a plan is answered by rtree_range_select.  Requests arriving while batches
+ * are in flight join the next batch a worker forms.
+ *
+ * Request kinds: RTREE_REQ_SELECT (range select of q query rectangles) and
+ * RTREE_REQ_PROBE_JOIN (join of q probe rectangles with the index).  Both
+ * replies are CSR in host memory: row i lists, ascending, the ids of indexed
+ * rectangles meeting query/probe i -- for a probe join, the pairs (i, id) in
+ * lexicographic order.  A reply's latency runs from submission until its
+ * results are in host memory.  submit and wait may be called from any host
+ * threads; the tree must outlive the server.
+ */
+enum { RTREE_REQ_SELECT = 0, RTREE_REQ_PROBE_JOIN = 1 };
+
+typedef struct rtree_server_config {
+    int32_t workers;           /* concurrent batches (streams); 0 -> 2 */
+    int32_t max_batch_queries; /* per batch; 0 -> 16384 */
+    int64_t max_batch_ids;     /* output ids per batch (the memory budget); 0 -> 16M */
+    int32_t mapping;           /* RTREE_MAP_* for the batches */
+    int32_t reserved[5];
+} rtree_server_config_t;
+
+typedef struct rtree_reply {
+    int32_t kind;
+    int32_t reserved;
+    int64_t rows;       /* queries or probes in the request */
+    int64_t total;      /* ids */
+    int64_t *offsets;   /* host, rows+1 */
+    int32_t *ids;       /* host, total */
+    double latency_us;  /* submission to results in host memory */
+} rtree_reply_t;
+
+typedef struct rtree_server_stats {
+    int64_t completed;     /* requests answered since start/reset */
+    int64_t batches;
+    int64_t batch_queries; /* queries run in batches */
+    int64_t splits;        /* batches split after an overflow */
+    int64_t fallbacks;     /* requests answered by rtree_range_select */
+    int64_t pending;       /* requests waiting now */
+    double p50_us, p99_us, max_us;
+    double elapsed_s;      /* since start/reset */
+} rtree_server_stats_t;
+
+typedef struct rtree_server rtree_server_t;
+RTREE_API rtree_status rtree_server_start(const rtree_t *tree, const rtree_server_config_t *cfg,
+                                          rtree_server_t **out);
+/* Copies the q rectangles (host memory); *ticket identifies the reply. */
+RTREE_API rtree_status rtree_server_submit(rtree_server_t *server, const float *rects, int64_t q,
+                                           int32_t kind, uint64_t *ticket);
+/* Waits for a reply (timeout_us < 0: no limit; RTREE_ETIMEOUT otherwise).
+ * Fills *reply; free its arrays with rtree_reply_free.  Each ticket's reply
+ * can be taken once. */
+RTREE_API rtree_status rtree_server_wait(rtree_server_t *server, uint64_t ticket, int64_t timeout_us,
+                                         rtree_reply_t *reply);
+RTREE_API void rtree_reply_free(rtree_reply_t *reply);
+RTREE_API rtree_status rtree_server_get_stats(rtree_server_t *server, rtree_server_stats_t *stats);
+RTREE_API rtree_status rtree_server_reset_stats(rtree_server_t *server);
+/* Answers every request already submitted, then stops the workers. */
+RTREE_API void rtree_server_stop(rtree_server_t *server);
+
+/*
  * rtree_range_select_noalloc -- range select that allocates no device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

@@ -44,6 +44,27 @@ class rtree_select_opts_t(C.Structure):
     _fields_ = [("unsorted", C.c_int32), ("mapping", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
+class rtree_server_config_t(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_batch_queries", C.c_int32),
+                ("max_batch_ids", C.c_int64), ("mapping", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class rtree_reply_t(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("rows", C.c_int64),
+                ("total", C.c_int64), ("offsets", C.POINTER(C.c_int64)),
+                ("ids", C.POINTER(C.c_int32)), ("latency_us", C.c_double)]
+
+
+class rtree_server_stats_t(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("batches", C.c_int64), ("batch_queries", C.c_int64),
+                ("splits", C.c_int64), ("fallbacks", C.c_int64), ("pending", C.c_int64),
+                ("p50_us", C.c_double), ("p99_us", C.c_double), ("max_us", C.c_double),
+                ("elapsed_s", C.c_double)]
+
+
+RTREE_REQ_SELECT, RTREE_REQ_PROBE_JOIN = 0, 1
+
+
 class rtree_info_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("levels", C.c_int32),
                 ("fanout", C.c_int32), ("layout", C.c_int32), ("device", C.c_int32),
@@ -79,6 +100,13 @@ def _bind(lib):
         "rtree_plan_offsets": (vp, [vp]),
         "rtree_plan_ids": (vp, [vp]),
         "rtree_plan_free": (None, [vp]),
+        "rtree_server_start": (C.c_int, [vp, C.POINTER(rtree_server_config_t), C.POINTER(vp)]),
+        "rtree_server_submit": (C.c_int, [vp, vp, i64, C.c_int32, C.POINTER(C.c_uint64)]),
+        "rtree_server_wait": (C.c_int, [vp, C.c_uint64, i64, C.POINTER(rtree_reply_t)]),
+        "rtree_reply_free": (None, [C.POINTER(rtree_reply_t)]),
+        "rtree_server_get_stats": (C.c_int, [vp, C.POINTER(rtree_server_stats_t)]),
+        "rtree_server_reset_stats": (C.c_int, [vp]),
+        "rtree_server_stop": (None, [vp]),
         "rtree_timing_enable": (None, [C.c_int]),
         "rtree_timing_reset": (None, []),
         "rtree_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
@@ -338,6 +366,55 @@ def rtree_plan_free(plan: int) -> None:
         load_library().rtree_plan_free(plan)
 
 
+def rtree_server_start(handle: int, workers: int = 2, max_batch_queries: int = 16384,
+                       max_batch_ids: int = 16 << 20, mapping: str | int = "auto") -> int:
+    lib = load_library()
+    cfg = rtree_server_config_t()
+    cfg.workers, cfg.max_batch_queries, cfg.max_batch_ids = workers, max_batch_queries, max_batch_ids
+    cfg.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
+    out = C.c_void_p()
+    _check(lib.rtree_server_start(handle, C.byref(cfg), C.byref(out)), lib)
+    return out.value
+
+
+def rtree_server_submit(server: int, rects, kind: int = RTREE_REQ_SELECT) -> int:
+    lib = load_library()
+    a = np.ascontiguousarray(rects, dtype=np.float32).reshape(-1, 4)
+    t = C.c_uint64()
+    _check(lib.rtree_server_submit(server, a.ctypes.data or None, a.shape[0], int(kind), C.byref(t)), lib)
+    return t.value
+
+
+def rtree_server_wait(server: int, ticket: int, timeout_us: int = -1):
+    """Returns (offsets int64[rows+1], ids int32[total], latency_us)."""
+    lib = load_library()
+    r = rtree_reply_t()
+    _check(lib.rtree_server_wait(server, int(ticket), int(timeout_us), C.byref(r)), lib)
+    try:
+        off = np.ctypeslib.as_array(r.offsets, shape=(r.rows + 1,)).copy()
+        ids = np.ctypeslib.as_array(r.ids, shape=(r.total,)).copy() if r.total else np.zeros(0, np.int32)
+        return off, ids, r.latency_us
+    finally:
+        lib.rtree_reply_free(C.byref(r))
+
+
+def rtree_server_get_stats(server: int) -> dict:
+    lib = load_library()
+    st = rtree_server_stats_t()
+    _check(lib.rtree_server_get_stats(server, C.byref(st)), lib)
+    return {k: getattr(st, k) for k, _ in rtree_server_stats_t._fields_}
+
+
+def rtree_server_reset_stats(server: int) -> None:
+    lib = load_library()
+    _check(lib.rtree_server_reset_stats(server), lib)
+
+
+def rtree_server_stop(server: int) -> None:
+    if server:
+        load_library().rtree_server_stop(server)
+
+
 def rtree_timing_enable(on: bool = True) -> None:
     load_library().rtree_timing_enable(1 if on else 0)
 
@@ -454,6 +531,36 @@ class Plan:
 
     def to_numpy(self):
         return self.offsets_tensor().cpu().numpy(), self.ids_tensor().cpu().numpy()
+
+
+class Server:
+    """Continuous-batching request loop over a resident tree (keeps it alive)."""
+
+    def __init__(self, tree: "RTree", workers: int = 2, max_batch_queries: int = 16384,
+                 max_batch_ids: int = 16 << 20, mapping="auto"):
+        self.tree = tree
+        self.handle = None
+        self.handle = rtree_server_start(tree.handle, workers, max_batch_queries, max_batch_ids, mapping)
+
+    def submit(self, rects, kind: int = RTREE_REQ_SELECT) -> int:
+        return rtree_server_submit(self.handle, rects, kind)
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        return rtree_server_wait(self.handle, ticket, timeout_us)
+
+    def stats(self) -> dict:
+        return rtree_server_get_stats(self.handle)
+
+    def reset_stats(self) -> None:
+        rtree_server_reset_stats(self.handle)
+
+    def stop(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            rtree_server_stop(h)
+
+    def __del__(self):
+        self.stop()
 
 
 class RTree:

@@ -52,14 +52,19 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_2309_16913_gb300 import rtree as rt
     src = tmp_path / "sizes.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rtree.h"\n'
-                   "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(rtree_config_t),"
+                   "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(rtree_config_t),"
                    " sizeof(rtree_select_opts_t), sizeof(rtree_info_t), offsetof(rtree_info_t, device_bytes),"
-                   " offsetof(rtree_info_t, root_mbr)); return 0;}\n")
+                   " offsetof(rtree_info_t, root_mbr), sizeof(rtree_server_config_t),"
+                   " offsetof(rtree_server_config_t, max_batch_ids), sizeof(rtree_reply_t),"
+                   " offsetof(rtree_reply_t, latency_us), sizeof(rtree_server_stats_t)); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(rt.rtree_config_t), C.sizeof(rt.rtree_select_opts_t), C.sizeof(rt.rtree_info_t),
-            rt.rtree_info_t.device_bytes.offset, rt.rtree_info_t.root_mbr.offset]
+            rt.rtree_info_t.device_bytes.offset, rt.rtree_info_t.root_mbr.offset,
+            C.sizeof(rt.rtree_server_config_t), rt.rtree_server_config_t.max_batch_ids.offset,
+            C.sizeof(rt.rtree_reply_t), rt.rtree_reply_t.latency_us.offset,
+            C.sizeof(rt.rtree_server_stats_t)]
     assert got == want
 
 
