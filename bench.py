@@ -48,8 +48,10 @@ def parse_args():
     ap.add_argument("--fanout", type=int, default=0, help="0: pick by timing 16/32/64")
     ap.add_argument("--layout", choices=["soa", "aos", "auto"], default="auto")
     ap.add_argument("--mapping", choices=["warp_per_query", "work_queue", "auto"], default="auto")
-    ap.add_argument("--n", type=int, default=None, help="override rectangles (testing only)")
-    ap.add_argument("--q", type=int, default=None, help="override queries (testing only)")
+    ap.add_argument("--rects", "--n", dest="n", type=int, default=None,
+                    help="override rectangles (testing only)")
+    ap.add_argument("--queries", "--q", dest="q", type=int, default=None,
+                    help="override queries (testing only)")
     ap.add_argument("--sel", type=float, nargs=2, default=None, metavar=("LO", "HI"),
                     help="override the query selectivity range (profiling a smaller index "
                          "with the full-size hit-count mix)")
@@ -253,24 +255,18 @@ def run_ours(args):
         return total
 
     # ---- pick fanout/layout by timing one step each (untimed for the result)
+    # pick fanout / layout / mapping with the library's autotuner (one
+    # build + sorted select per configuration, CUDA-event timed)
     fanouts = [args.fanout] if args.fanout else [16, 32, 64]
-    layouts = ["soa", "aos"] if args.layout == "auto" else [args.layout]
-    mappings = ["warp_per_query", "work_queue"] if args.mapping == "auto" else [args.mapping]
-    sweep = {}
-    total_hits = None
-    step(fanouts[0], layouts[0], mappings[0])  # first touch / pool growth
-    for F in fanouts:
-        for lay in layouts:
-            for mp in mappings:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                total_hits = step(F, lay, mp)
-                torch.cuda.synchronize()
-                sweep[f"F{F}_{lay}_{mp}"] = round((time.perf_counter() - t0) * 1e3, 3)
+    tune = rt.rtree_autotune(rects, queries, ids, fanouts=fanouts, include_build=True, stream=stream)
+    sweep = {k: v for k, v in tune["all"].items()
+             if (args.layout == "auto" or f"_{args.layout}_" in k)
+             and (args.mapping == "auto" or k.endswith(args.mapping))}
     best = min(sweep, key=sweep.get)
     F = int(best.split("_")[0][1:])
     layout = best.split("_")[1]
     mapping = best.split("_", 2)[2]
+    total_hits = step(F, layout, mapping)
 
     for _ in range(args.warmup):
         step(F, layout, mapping)

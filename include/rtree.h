@@ -346,6 +346,33 @@ RTREE_API const char *rtree_last_error(void);
 RTREE_API const char *rtree_version(void);
 
 /*
+ * rtree_autotune -- choose fanout, node layout and thread mapping by timing.
+ *
+ * Builds a tree over rects/ids for every fanout in fanouts[0 .. n_fanouts)
+ * (NULL or 0 -> {16, 32, 64}; at most 8) and both layouts, and times a
+ * sorted rtree_range_select of the q queries under both mappings with CUDA
+ * events on `stream` (one untimed run first).  flags & RTREE_TUNE_INCLUDE_BUILD
+ * adds the build time to each configuration's time.  *out receives the
+ * fastest configuration and every configuration's time (at most 32).  Inputs
+ * may be host or device memory; callers pass a representative sample.
+ */
+enum { RTREE_TUNE_INCLUDE_BUILD = 1 };
+
+typedef struct rtree_tune_result {
+    int32_t fanout, layout, mapping, tried;
+    double ms;              /* time of the chosen configuration */
+    double ms_all[32];      /* every configuration tried, in order */
+    int32_t fanout_all[32];
+    int32_t layout_all[32];
+    int32_t mapping_all[32];
+} rtree_tune_result_t;
+
+RTREE_API rtree_status rtree_autotune(const float *rects, const int32_t *ids, int64_t n,
+                                      const float *queries, int64_t q, const int32_t *fanouts,
+                                      int32_t n_fanouts, int32_t flags, void *stream,
+                                      rtree_tune_result_t *out);
+
+/*
  * Kernel accounting.  Every kernel launch the library makes is counted under
  * a short name ("select_count", "sort_mid", ...).  With timing enabled, CUDA
  * events recorded on the launching stream bracket each launch and their

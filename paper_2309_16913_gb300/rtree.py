@@ -63,6 +63,14 @@ class rtree_server_stats_t(C.Structure):
 
 
 RTREE_REQ_SELECT, RTREE_REQ_PROBE_JOIN = 0, 1
+RTREE_TUNE_INCLUDE_BUILD = 1
+
+
+class rtree_tune_result_t(C.Structure):
+    _fields_ = [("fanout", C.c_int32), ("layout", C.c_int32), ("mapping", C.c_int32),
+                ("tried", C.c_int32), ("ms", C.c_double), ("ms_all", C.c_double * 32),
+                ("fanout_all", C.c_int32 * 32), ("layout_all", C.c_int32 * 32),
+                ("mapping_all", C.c_int32 * 32)]
 
 
 class rtree_info_t(C.Structure):
@@ -107,6 +115,8 @@ def _bind(lib):
         "rtree_server_get_stats": (C.c_int, [vp, C.POINTER(rtree_server_stats_t)]),
         "rtree_server_reset_stats": (C.c_int, [vp]),
         "rtree_server_stop": (None, [vp]),
+        "rtree_autotune": (C.c_int, [vp, vp, i64, vp, i64, vp, C.c_int32, C.c_int32, vp,
+                                     C.POINTER(rtree_tune_result_t)]),
         "rtree_timing_enable": (None, [C.c_int]),
         "rtree_timing_reset": (None, []),
         "rtree_timing_get": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
@@ -413,6 +423,28 @@ def rtree_server_reset_stats(server: int) -> None:
 def rtree_server_stop(server: int) -> None:
     if server:
         load_library().rtree_server_stop(server)
+
+
+def rtree_autotune(rects, queries, ids=None, fanouts=(16, 32, 64), include_build: bool = True,
+                   stream=None) -> dict:
+    """Times every fanout x layout x mapping on the given sample and returns
+    the fastest configuration plus all times (see the C header)."""
+    lib = load_library()
+    rp, n, keep_r = _as_rows(rects, "rects")
+    ip, keep_i = _as_ids(ids, n)
+    qp, q, keep_q = _as_rows(queries, "queries")
+    fo = (C.c_int32 * len(fanouts))(*fanouts)
+    out = rtree_tune_result_t()
+    _check(lib.rtree_autotune(rp, ip, n, qp, q, fo, len(fanouts),
+                              RTREE_TUNE_INCLUDE_BUILD if include_build else 0, _stream(stream),
+                              C.byref(out)), lib)
+    del keep_r, keep_i, keep_q
+    names = {v: k for k, v in MAPPINGS.items()}
+    lays = {v: k for k, v in LAYOUTS.items()}
+    return {"fanout": out.fanout, "layout": lays[out.layout], "mapping": names[out.mapping],
+            "ms": out.ms,
+            "all": {f"F{out.fanout_all[i]}_{lays[out.layout_all[i]]}_{names[out.mapping_all[i]]}":
+                    round(out.ms_all[i], 3) for i in range(out.tried)}}
 
 
 def rtree_timing_enable(on: bool = True) -> None:

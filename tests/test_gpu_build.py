@@ -99,3 +99,18 @@ def test_injected_allocation_failures_recover(rt):
             off, ids = res.to_numpy()
             res.close()
         assert np.array_equal(off, want[0]) and np.array_equal(ids, want[1])
+
+
+def test_autotune_returns_a_measured_choice(rt):
+    w = dg.workload("scaled", n=300_000, q=4000)
+    tune = rt.rtree_autotune(w.rects, w.queries, w.ids, fanouts=(16, 64))
+    assert len(tune["all"]) == 2 * 2 * 2
+    key = f"F{tune['fanout']}_{tune['layout']}_{tune['mapping']}"
+    assert tune["all"][key] == min(tune["all"].values()) and tune["ms"] > 0
+    # the chosen configuration still answers exactly
+    want = oracle.Tree(w.rects, w.ids, tune["fanout"]).select(w.queries[:500])
+    with rt.RTree(w.rects, w.ids, fanout=tune["fanout"], layout=tune["layout"]) as t:
+        res = t.range_select(w.queries[:500], mapping=tune["mapping"])
+        off, ids = res.to_numpy()
+        res.close()
+    assert np.array_equal(off, want[0]) and np.array_equal(ids, want[1])
