@@ -9,9 +9,10 @@
 //                 swaps inside a lane);
 //   257..16384    one CTA of 128-1024 threads, entirely in shared memory:
 //                 bucket the keys by their top differing bits (2-4 keys per
-//                 bucket for spread-out ids) with shared atomics and
-//                 insertion-sort each bucket; a crowded bucket sends the
-//                 segment to a stable LSD radix sort (8-bit digits);
+//                 bucket for spread-out ids) with shared atomics, then each
+//                 thread sorts whole buckets in registers with a bitonic
+//                 network; a crowded bucket sends the segment to a stable
+//                 LSD radix sort (8-bit digits);
 //   > 16384       gathered into place, partitioned by its top differing bits
 //                 into buckets of about 8K ids (MSD step through a scratch
 //                 area), each bucket then sorted like a mid-size segment.
@@ -32,6 +33,7 @@ constexpr int kItems = 16;              // keys per thread in the CTA sort
 constexpr int kCtaMax = 1024 * kItems;  // 16384: largest in-shared-memory segment
 constexpr uint32_t kSign = 0x80000000u;
 constexpr int kBucketBitsMax = 12;      // at most 4096 buckets
+constexpr int kBucketDensity = 2;       // buckets = 2^(ceil(log2 n) - 2): 2-4 keys each
 constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to LSD
 
 // Segment classes (index into the class lists).
@@ -276,39 +278,49 @@ __device__ __forceinline__ int block_scan_int(CtaSmem<THREADS> &sm, int v, int *
     return before + inc - v;
 }
 
-// The CTA copies segment i's ids into sm.buf[0 .. n), flipped to keys.
+// The CTA copies segment i's ids into sm.buf[0 .. n), flipped to keys.  The
+// first chunk of range descriptors is requested before the leaf hits are
+// copied, so both loads are in flight together.
 template <int THREADS>
 __device__ __forceinline__ void cta_gather(CtaSmem<THREADS> &sm, const SortSources &S, int64_t i)
 {
     constexpr int W = THREADS / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
-    for (int64_t e = l0 + threadIdx.x; e < l1; e += THREADS)
-        sm.buf[e - l0] = (uint32_t)S.leaf[e] ^ kSign;
-    int pos = (int)(l1 - l0);
+    int64_t r0 = 0, r1 = 0;
     if (S.rng) {
-        const int64_t r0 = S.off_rng[i], r1 = S.off_rng[i + 1];
-        for (int64_t rb = r0; rb < r1; rb += THREADS) {
-            const int64_t r = rb + threadIdx.x;
-            int2 rg = make_int2(0, 0);
-            if (r < r1)
-                rg = S.rng[r];
-            const int len = rg.y - rg.x;
-            int total;
-            const int start = block_scan_int<THREADS>(sm, len, &total);
-            sm.rlo[threadIdx.x] = rg.x;
-            sm.rlen[threadIdx.x] = len;
-            sm.rstart[threadIdx.x] = pos + start;
-            __syncthreads();
-            const int cnt = (int)(r1 - rb < THREADS ? r1 - rb : THREADS);
-            for (int k = w; k < cnt; k += W) {  // warp w copies ranges w, w+W, ...
-                const int lo = sm.rlo[k], ln = sm.rlen[k], st = sm.rstart[k];
-                for (int e = lane; e < ln; e += 32)
-                    sm.buf[st + e] = (uint32_t)__ldg(S.tree_ids + lo + e) ^ kSign;
-            }
-            pos += total;
-            __syncthreads();
+        r0 = S.off_rng[i];
+        r1 = S.off_rng[i + 1];
+    }
+    int2 rg = make_int2(0, 0);
+    if (r0 + threadIdx.x < r1)
+        rg = S.rng[r0 + threadIdx.x];
+    const int nl = (int)(l1 - l0);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < nl; e += THREADS)
+        sm.buf[e] = (uint32_t)S.leaf[l0 + e] ^ kSign;
+    int pos = nl;
+    for (int64_t rb = r0; rb < r1; rb += THREADS) {
+        if (rb != r0) {
+            rg = make_int2(0, 0);
+            if (rb + threadIdx.x < r1)
+                rg = S.rng[rb + threadIdx.x];
         }
+        const int len = rg.y - rg.x;
+        int total;
+        const int start = block_scan_int<THREADS>(sm, len, &total);
+        sm.rlo[threadIdx.x] = rg.x;
+        sm.rlen[threadIdx.x] = len;
+        sm.rstart[threadIdx.x] = pos + start;
+        __syncthreads();
+        const int cnt = (int)(r1 - rb < THREADS ? r1 - rb : THREADS);
+        for (int k = w; k < cnt; k += W) {  // warp w copies ranges w, w+W, ...
+            const int lo = sm.rlo[k], ln = sm.rlen[k], st = sm.rstart[k];
+            for (int e = lane; e < ln; e += 32)
+                sm.buf[st + e] = (uint32_t)__ldg(S.tree_ids + lo + e) ^ kSign;
+        }
+        pos += total;
+        __syncthreads();
     }
     __syncthreads();
 }
@@ -349,10 +361,42 @@ __device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_
     return a_and ^ a_or;
 }
 
+// Sorts buf[s0 .. s0+c), c <= N, in registers: a bitonic network over N
+// values padded with the largest key (the first c outputs are then exactly
+// the sorted bucket, whatever equal keys it holds).
+template <int N>
+__device__ __forceinline__ void bucket_network(uint32_t *buf, int s0, int c)
+{
+    uint32_t v[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        v[k] = k < c ? buf[s0 + k] : 0xffffffffu;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int m = k ^ stride;
+                if (m > k) {
+                    const bool up = (k & size) == 0;
+                    const uint32_t a = v[k], b = v[m];
+                    v[k] = up ? min(a, b) : max(a, b);
+                    v[m] = up ? max(a, b) : min(a, b);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (k < c)
+            buf[s0 + k] = v[k];
+}
+
 // Sorts the n <= THREADS*kItems keys in sm.buf and writes them to dst (xor
-// kSign back to ids).  Keys are bucketed by their top B differing bits (B
-// about log2(n) - 1, at most 12) with shared atomics, then each bucket is
-// insertion-sorted; the order inside a bucket before that does not matter.
+// kSign back to ids).  Keys are bucketed by their top B differing bits (B =
+// ceil(log2 n) - 2, at most 12) with shared atomics, so a bucket holds two to
+// four keys on average; each bucket is then sorted in registers.
 // Returns false, having written the unsorted ids to dst, if a bucket holds
 // more than kBucketCrowded keys (the caller then sorts dst with LSD).
 template <int THREADS>
@@ -381,7 +425,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         return true;
     }
     const int hb = 31 - __clz(diff);
-    int bits = (32 - __clz((unsigned)(n - 1))) - 1;  // ceil(log2 n) - 1
+    int bits = (32 - __clz((unsigned)(n - 1))) - kBucketDensity;
     bits = bits < 1 ? 1 : (bits > kBucketBitsMax ? kBucketBitsMax : bits);
     if (bits > hb + 1)
         bits = hb + 1;
@@ -434,19 +478,26 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         }
     }
     __syncthreads();
-    // cnt[b] is now the end of bucket b; sort each bucket by insertion
-    for (int b = threadIdx.x; b < nb; b += THREADS) {
-        const int e = (int)sm.cnt[b];
-        const int s0 = b ? (int)sm.cnt[b - 1] : 0;
-        for (int i = s0 + 1; i < e; ++i) {
-            const uint32_t x = sm.buf[i];
-            int j = i - 1;
-            while (j >= s0 && sm.buf[j] > x) {
-                sm.buf[j + 1] = sm.buf[j];
-                --j;
-            }
-            sm.buf[j + 1] = x;
+    // cnt[b] is now the end of bucket b.  Each thread sorts whole buckets in
+    // registers with a sorting network sized to the warp's largest bucket.
+    for (int b0 = threadIdx.x - (threadIdx.x & 31); b0 < nb; b0 += THREADS) {
+        const int b = b0 + (threadIdx.x & 31);
+        int s0 = 0, c = 0;
+        if (b < nb) {
+            s0 = b ? (int)sm.cnt[b - 1] : 0;
+            c = (int)sm.cnt[b] - s0;
         }
+        const int cmax = __reduce_max_sync(RT_FULL, c);
+        if (cmax <= 1)
+            continue;
+        if (cmax <= 4)
+            bucket_network<4>(sm.buf, s0, c);
+        else if (cmax <= 8)
+            bucket_network<8>(sm.buf, s0, c);
+        else if (cmax <= 16)
+            bucket_network<16>(sm.buf, s0, c);
+        else
+            bucket_network<32>(sm.buf, s0, c);
     }
     __syncthreads();
     for (int p = threadIdx.x; p < n; p += THREADS)
