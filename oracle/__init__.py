@@ -45,6 +45,14 @@ def _bind(lib):
     i64, i32p, f32p, i64p = C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_int64)
     lib.orc_tree_build.restype = C.c_void_p
     lib.orc_tree_build.argtypes = [f32p, i32p, i64, C.c_int]
+    lib.orc_tree_build2.restype = C.c_void_p
+    lib.orc_tree_build2.argtypes = [f32p, i32p, i64, C.c_int, C.c_int]
+    lib.orc_join_pruned.restype = i64
+    lib.orc_join_pruned.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(i32p), i64p]
+    lib.orc_join_tests.restype = i64
+    lib.orc_join_tests.argtypes = [C.c_void_p, C.c_void_p]
+    lib.orc_o5_bounds.restype = C.c_int
+    lib.orc_o5_bounds.argtypes = [f32p, C.c_int, f32p, C.c_int, i32p, i32p, i32p]
     lib.orc_tree_free.restype = None
     lib.orc_tree_free.argtypes = [C.c_void_p]
     lib.orc_tree_levels.restype = C.c_int
@@ -114,15 +122,20 @@ def _take_i32(lib, ptr, count) -> np.ndarray:
 
 
 class Tree:
-    """Oracle R-tree: STR bulk load, recursive select, synchronized join."""
+    """Oracle R-tree: STR bulk load, recursive select, synchronized join.
 
-    def __init__(self, rects, ids=None, fanout: int = 16, lib=None):
+    ``sort_children`` orders every node's entries by ascending lx (stable),
+    as the join pruning of Section 4.2 assumes."""
+
+    def __init__(self, rects, ids=None, fanout: int = 16, lib=None, sort_children: bool = False):
         self._lib = lib or load()
         self.rects = _rects(rects)
         self.n = self.rects.shape[0]
         self.ids = _ids(ids, self.n)
         self.fanout = int(fanout)
-        h = self._lib.orc_tree_build(_f(self.rects), _i(self.ids), self.n, self.fanout)
+        self.sort_children = bool(sort_children)
+        h = self._lib.orc_tree_build2(_f(self.rects), _i(self.ids), self.n, self.fanout,
+                                      1 if self.sort_children else 0)
         if not h:
             raise MemoryError("oracle tree build failed")
         self._h = h
@@ -158,6 +171,20 @@ class Tree:
         if total < 0:
             raise MemoryError("oracle join failed")
         return _take_i32(self._lib, ptr, 2 * total).reshape(-1, 2)
+
+    def join_pruned(self, other: "Tree"):
+        """Join with the O3/O4 prunings (both trees built with sort_children).
+        Returns (pairs int32[total, 2] sorted, predicate evaluations)."""
+        ptr = C.POINTER(C.c_int32)()
+        tests = C.c_int64()
+        total = self._lib.orc_join_pruned(self._h, other._h, C.byref(ptr), C.byref(tests))
+        if total < 0:
+            raise ValueError("oracle pruned join needs two trees built with sort_children")
+        return _take_i32(self._lib, ptr, 2 * total).reshape(-1, 2), tests.value
+
+    def join_tests(self, other: "Tree") -> int:
+        """Predicate evaluations of the plain synchronized join."""
+        return self._lib.orc_join_tests(self._h, other._h)
 
     def export(self):
         """Level-major export, root level first (see orc_tree_export)."""
@@ -197,3 +224,23 @@ def brute_join(r_rects, s_rects, r_ids=None, s_ids=None, lib=None):
     if total < 0:
         raise MemoryError("oracle brute join failed")
     return _take_i32(lib, ptr, 2 * total).reshape(-1, 2)
+
+
+def o5_bounds(out_hx, in_lx, lib=None):
+    """The O5 search of Section 4.2 (see orc_o5_bounds).  Returns (flip
+    int32[n_out], gather indices int32[rounds, n_out], flip indices after
+    each round int32[rounds, n_out] with -1 for undefined)."""
+    lib = lib or load()
+    o = np.ascontiguousarray(out_hx, dtype=np.float32)
+    i = np.ascontiguousarray(in_lx, dtype=np.float32)
+    n_out, n_in = o.shape[0], i.shape[0]
+    rounds_max = 1
+    while (1 << (rounds_max - 1)) < max(n_in, 1):
+        rounds_max += 1
+    flip = np.zeros(max(n_out, 1), np.int32)
+    tg = np.zeros((rounds_max, max(n_out, 1)), np.int32)
+    tf = np.zeros((rounds_max, max(n_out, 1)), np.int32)
+    rounds = lib.orc_o5_bounds(_f(o), n_out, _f(i), n_in, _i(flip), _i(tg), _i(tf))
+    if rounds < 0:
+        raise MemoryError("oracle O5 failed")
+    return flip[:n_out], tg[:rounds, :n_out], tf[:rounds, :n_out]

@@ -109,6 +109,7 @@ typedef struct onode {
 
 typedef struct {
     int fanout;
+    int sorted; /* entries of every node ascending by lx (Section 4.2 pruning) */
     int levels; /* 0 for an empty tree */
     int64_t n;
     onode *root;
@@ -229,8 +230,39 @@ void orc_tree_free(otree *t)
     free(t);
 }
 
+/*
+ * Section 4.2 assumes the entries of every node are ordered by one MBR key,
+ * lx.  With sort_children set, each node's entries are put in ascending lx
+ * order once the node is packed (equal lx, including -0 against +0, keep
+ * their packing order): an insertion sort, so it is stable.  Which items
+ * share a node, and so every node MBR, is unchanged.
+ */
+static void sort_entries_by_lx(onode *nd)
+{
+    for (int e = 1; e < nd->count; e++) {
+        box b = nd->mbr[e];
+        int32_t id = nd->height == 0 ? nd->id[e] : 0;
+        onode *ch = nd->height == 0 ? NULL : nd->child[e];
+        int k = e - 1;
+        while (k >= 0 && nd->mbr[k].lx > b.lx) {
+            nd->mbr[k + 1] = nd->mbr[k];
+            if (nd->height == 0)
+                nd->id[k + 1] = nd->id[k];
+            else
+                nd->child[k + 1] = nd->child[k];
+            k--;
+        }
+        nd->mbr[k + 1] = b;
+        if (nd->height == 0)
+            nd->id[k + 1] = id;
+        else
+            nd->child[k + 1] = ch;
+    }
+}
+
 /* Bulk-load with STR.  rects: n x [xmin, ymin, xmax, ymax]; ids: n. */
-otree *orc_tree_build(const float *rects, const int32_t *ids, int64_t n, int fanout)
+otree *orc_tree_build2(const float *rects, const int32_t *ids, int64_t n, int fanout,
+                       int sort_children)
 {
     if (fanout < 2 || n < 0)
         return NULL;
@@ -238,6 +270,7 @@ otree *orc_tree_build(const float *rects, const int32_t *ids, int64_t n, int fan
     if (!t)
         return NULL;
     t->fanout = fanout;
+    t->sorted = sort_children != 0;
     t->n = n;
     if (n == 0)
         return t;
@@ -302,6 +335,8 @@ otree *orc_tree_build(const float *rects, const int32_t *ids, int64_t n, int fan
                 else
                     nd->child[r - lo] = items[it];
             }
+            if (t->sorted)
+                sort_entries_by_lx(nd);
             nb[k] = node_mbr(nd);
         }
         free(order);
@@ -331,6 +366,11 @@ fail:
     free(items);
     orc_tree_free(t);
     return NULL;
+}
+
+otree *orc_tree_build(const float *rects, const int32_t *ids, int64_t n, int fanout)
+{
+    return orc_tree_build2(rects, ids, n, fanout, 0);
 }
 
 int orc_tree_levels(const otree *t) { return t ? t->levels : 0; }
@@ -512,6 +552,177 @@ int64_t orc_join(const otree *r, const otree *s, int32_t **pairs_out)
     qsort(out.v, (size_t)(out.n / 2), 2 * sizeof(int32_t), cmp_pair);
     *pairs_out = out.v;
     return out.n / 2;
+}
+
+/* --------------------------------------------- join with sorted-node pruning */
+
+/*
+ * The one-to-many join of Section 4.1 with the two prunings of Section 4.2,
+ * for trees whose node entries ascend by lx:
+ *   O3 -- outer children are taken in ascending lx.  If the key test
+ *         out.lx <= in.hx fails against every inner child, no later outer
+ *         child (whose lx is no smaller) can pass it: the rest of the outer
+ *         node is skipped.
+ *   O4 -- for one outer child, inner children are scanned in ascending lx;
+ *         the first with in.lx > out.hx ends the scan, as every later inner
+ *         child starts even further right.
+ * Where heights differ, the taller side's children are scanned in ascending
+ * lx against the other node's MBR and the scan ends at the first child that
+ * starts right of it (O4 with a single outer MBR).  *tests counts the full
+ * predicate evaluations, to show what the pruning saves.
+ */
+static int join_rec_pruned(const onode *a, box amb, const onode *b, box bmb, ivec *out,
+                           int64_t *tests)
+{
+    if (a->height == b->height) {
+        for (int i = 0; i < a->count; i++) {
+            int any = 0; /* O3: the lx key test against all inner children */
+            for (int j = 0; j < b->count; j++)
+                if (a->mbr[i].lx <= b->mbr[j].hx)
+                    any = 1;
+            if (!any)
+                break;
+            for (int j = 0; j < b->count; j++) {
+                if (b->mbr[j].lx > a->mbr[i].hx) /* O4 */
+                    break;
+                (*tests)++;
+                if (!intersects(a->mbr[i], b->mbr[j]))
+                    continue;
+                if (a->height == 0) {
+                    if (emit_pair(out, a->id[i], b->id[j]))
+                        return -1;
+                } else if (join_rec_pruned(a->child[i], a->mbr[i], b->child[j], b->mbr[j], out,
+                                           tests)) {
+                    return -1;
+                }
+            }
+        }
+    } else if (a->height > b->height) {
+        for (int i = 0; i < a->count; i++) {
+            if (a->mbr[i].lx > bmb.hx)
+                break;
+            (*tests)++;
+            if (intersects(a->mbr[i], bmb) &&
+                join_rec_pruned(a->child[i], a->mbr[i], b, bmb, out, tests))
+                return -1;
+        }
+    } else {
+        for (int j = 0; j < b->count; j++) {
+            if (b->mbr[j].lx > amb.hx)
+                break;
+            (*tests)++;
+            if (intersects(amb, b->mbr[j]) &&
+                join_rec_pruned(a, amb, b->child[j], b->mbr[j], out, tests))
+                return -1;
+        }
+    }
+    return 0;
+}
+
+/* Same contract as orc_join; both trees must have been built with
+ * sort_children (else -1).  *tests receives the predicate evaluations. */
+int64_t orc_join_pruned(const otree *r, const otree *s, int32_t **pairs_out, int64_t *tests)
+{
+    ivec out = {0, 0, 0};
+    *tests = 0;
+    if (r && s && r->root && s->root) {
+        if (!r->sorted || !s->sorted)
+            return -1;
+        if (join_rec_pruned(r->root, r->root_mbr, s->root, s->root_mbr, &out, tests)) {
+            free(out.v);
+            return -1;
+        }
+    }
+    qsort(out.v, (size_t)(out.n / 2), 2 * sizeof(int32_t), cmp_pair);
+    *pairs_out = out.v;
+    return out.n / 2;
+}
+
+/* Predicate evaluations of the plain join (for comparison with the above). */
+static void count_rec(const onode *a, box amb, const onode *b, box bmb, int64_t *tests)
+{
+    if (a->height == b->height) {
+        for (int i = 0; i < a->count; i++)
+            for (int j = 0; j < b->count; j++) {
+                (*tests)++;
+                if (a->height > 0 && intersects(a->mbr[i], b->mbr[j]))
+                    count_rec(a->child[i], a->mbr[i], b->child[j], b->mbr[j], tests);
+            }
+    } else if (a->height > b->height) {
+        for (int i = 0; i < a->count; i++) {
+            (*tests)++;
+            if (intersects(a->mbr[i], bmb))
+                count_rec(a->child[i], a->mbr[i], b, bmb, tests);
+        }
+    } else {
+        for (int j = 0; j < b->count; j++) {
+            (*tests)++;
+            if (intersects(amb, b->mbr[j]))
+                count_rec(a, amb, b->child[j], b->mbr[j], tests);
+        }
+    }
+}
+
+int64_t orc_join_tests(const otree *r, const otree *s)
+{
+    int64_t tests = 0;
+    if (r && s && r->root && s->root)
+        count_rec(r->root, r->root_mbr, s->root, s->root_mbr, &tests);
+    return tests;
+}
+
+/*
+ * O5, the batched form of O4 (Section 4.2, many-to-many comparison): for
+ * every outer child at once, find the index beyond which the inner children
+ * (ascending lx) cannot qualify, i.e. the first inner index with
+ * in.lx > out.hx, by a search that all lanes run in step.
+ *   P = n_in rounded up to a power of two; every lane starts at gather index
+ *   g = P/2 with its flip index undefined (all inner children qualify);
+ *   each of the log2(P)+1 rounds compares out.hx >= in[g].lx (an index past
+ *   the node counts as failing); a failing lane records g as its flip index
+ *   (keeping the smallest), then every lane moves g up by the step if it
+ *   passed and down if it failed; the step starts at P/4 and halves each
+ *   round, but never below 1.
+ * flip[i] receives the bound for outer child i (n_in when every inner child
+ * qualifies).  If trace_g / trace_f are not NULL they receive, for every
+ * round, the gather indices used and the flip indices after the round
+ * (-1 = undefined), n_out per round.  Returns the number of rounds.
+ */
+int orc_o5_bounds(const float *out_hx, int n_out, const float *in_lx, int n_in, int32_t *flip,
+                  int32_t *trace_g, int32_t *trace_f)
+{
+    int P = 1, logp = 0;
+    while (P < n_in) {
+        P *= 2;
+        logp++;
+    }
+    for (int i = 0; i < n_out; i++)
+        flip[i] = -1;
+    int32_t *g = (int32_t *)malloc((size_t)(n_out > 0 ? n_out : 1) * sizeof(int32_t));
+    if (!g)
+        return -1;
+    for (int i = 0; i < n_out; i++)
+        g[i] = P / 2;
+    int step = P / 4 > 1 ? P / 4 : 1;
+    int rounds = logp + 1;
+    for (int t = 0; t < rounds; t++) {
+        for (int i = 0; i < n_out; i++) {
+            if (trace_g)
+                trace_g[t * n_out + i] = g[i];
+            int pass = g[i] >= 0 && g[i] < n_in && out_hx[i] >= in_lx[g[i]];
+            if (!pass && g[i] < n_in && (flip[i] < 0 || g[i] < flip[i]))
+                flip[i] = g[i];
+            g[i] = pass ? g[i] + step : g[i] - step;
+            if (trace_f)
+                trace_f[t * n_out + i] = flip[i];
+        }
+        step = step / 2 > 1 ? step / 2 : 1;
+    }
+    for (int i = 0; i < n_out; i++)
+        if (flip[i] < 0)
+            flip[i] = n_in;
+    free(g);
+    return rounds;
 }
 
 /* Brute-force join: every (r, s) pair. */

@@ -93,3 +93,13 @@ def str_case(name):
         mbrs[g, e] = v
     exp["mbrs"] = mbrs
     return F, np.array(rects, np.float32), np.array(ids, np.int32), exp
+
+
+def o5_case(name="o5_example.txt"):
+    """{key: np.ndarray} for the O5 worked example."""
+    out = {}
+    for line in _lines(name):
+        t = line.split()
+        dt = np.float32 if t[0] in ("IN_LX", "OUT_HX") else np.int32
+        out[t[0]] = np.array([_num(x) for x in t[1:]], dtype=dt)
+    return out

@@ -148,8 +148,102 @@ def check_random_vs_brute(lib, seeds=(0, 1), n=300, q=40):
                 assert np.array_equal(pb, pt), (kind, fr, fs, seed)
 
 
+def sorted_export_reference(e):
+    """From the export of a tree, the export of the same tree with every
+    node's entries stably reordered by ascending lx (written independently of
+    the oracle: NumPy over the exported arrays)."""
+    ln, counts, mbrs, leaf_ids = e["level_nodes"], e["counts"], e["mbrs"], e["leaf_ids"]
+    L = len(ln)
+    bases = np.concatenate([[0], np.cumsum(ln)]).astype(np.int64)
+    # children of each internal node / ids of each leaf, in export order
+    kids, leaf_of, nxt = {}, {}, {}
+    for lv in range(L):
+        ptr = 0
+        for k in range(ln[lv]):
+            g = bases[lv] + k
+            c = counts[g]
+            if lv < L - 1:
+                kids[g] = np.arange(bases[lv + 1] + ptr, bases[lv + 1] + ptr + c)
+            else:
+                leaf_of[g] = leaf_ids[ptr:ptr + c]
+            ptr += c
+    out_counts, out_mbrs, out_ids = [], [], []
+    level = [0] if L else []
+    for lv in range(L):
+        nxt = []
+        for g in level:
+            c = counts[g]
+            perm = np.argsort(mbrs[g, :c, 0], kind="stable")
+            m = mbrs[g].copy()
+            m[:c] = mbrs[g, :c][perm]
+            out_counts.append(c)
+            out_mbrs.append(m)
+            if lv < L - 1:
+                nxt.extend(kids[g][perm].tolist())
+            else:
+                out_ids.append(leaf_of[g][perm])
+        level = nxt
+    F = mbrs.shape[1]
+    return {"level_nodes": ln.copy(), "counts": np.array(out_counts, np.int32),
+            "mbrs": np.array(out_mbrs, np.float32).reshape(-1, F, 4),
+            "leaf_ids": np.concatenate(out_ids) if out_ids else leaf_ids.copy()}
+
+
+def check_sorted_build(lib):
+    for kind, n in (("grid", 257), ("dups", 300), ("uniform", 500), ("negative", 130)):
+        rects = random_case(kind, n, 5)
+        ids = np.arange(n, dtype=np.int32)[::-1].copy()
+        for F in (2, 3, 4, 16):
+            plain = oracle.Tree(rects, ids, F, lib=lib).export()
+            got = oracle.Tree(rects, ids, F, lib=lib, sort_children=True).export()
+            want = sorted_export_reference(plain)
+            for k in ("level_nodes", "counts", "leaf_ids", "mbrs"):
+                assert np.array_equal(got[k], want[k]), (kind, F, k)
+
+
+def check_pruned_join(lib):
+    saved = 0
+    for seed, kind in ((3, "grid"), (4, "uniform"), (5, "negative"), (6, "dups"), (7, "points")):
+        r = random_case(kind, 240, seed)
+        s = random_case(kind, 90, seed + 50)
+        rid = np.arange(240, dtype=np.int32)
+        sid = np.arange(90, dtype=np.int32) + 500
+        want = oracle.brute_join(r, s, rid, sid, lib=lib)
+        for fr, fs in ((2, 2), (4, 4), (3, 16), (16, 2)):
+            a = oracle.Tree(r, rid, fr, lib=lib, sort_children=True)
+            b = oracle.Tree(s, sid, fs, lib=lib, sort_children=True)
+            got, tests = a.join_pruned(b)
+            assert np.array_equal(got, want), (kind, fr, fs)
+            plain = oracle.Tree(r, rid, fr, lib=lib).join_tests(oracle.Tree(s, sid, fs, lib=lib))
+            assert tests <= plain, (kind, fr, fs, tests, plain)
+            saved += plain - tests
+    assert saved > 0
+    with pytest.raises(ValueError):  # unsorted trees are refused
+        oracle.Tree(r, rid, 4, lib=lib).join_pruned(oracle.Tree(s, sid, 4, lib=lib))
+
+
+def check_o5(lib):
+    g = golden_io.o5_case()
+    flip, tg, tf = oracle.o5_bounds(g["OUT_HX"], g["IN_LX"], lib=lib)
+    assert np.array_equal(tg[0], g["G1"]) and np.array_equal(tg[1], g["G2"])
+    assert np.array_equal(tf[0], g["F1"])
+    assert np.array_equal((g["OUT_HX"] >= g["IN_LX"][2]).astype(np.int32), g["MASK1"])
+    assert np.array_equal(flip, g["FLIP"]) and len(tg) == 3
+    # brute force: the bound is the number of inner lx <= out.hx
+    rng = np.random.default_rng(9)
+    for n_in in range(1, 18):
+        for _ in range(6):
+            in_lx = np.sort(rng.integers(0, 6, n_in).astype(np.float32))
+            out_hx = np.concatenate([rng.integers(-1, 7, 12).astype(np.float32), in_lx,
+                                     np.array([-INF, INF], np.float32)])
+            flip, tg, _ = oracle.o5_bounds(out_hx, in_lx, lib=lib)
+            want = np.searchsorted(in_lx, out_hx, side="right").astype(np.int32)
+            assert np.array_equal(flip, want), (in_lx, out_hx, flip, want)
+            assert len(tg) == int(np.ceil(np.log2(n_in))) + 1
+
+
 PIN_SUITE = (check_predicate, check_select_golden, check_join_golden, check_str_golden,
-             check_random_vs_brute)
+             check_random_vs_brute, check_sorted_build, check_pruned_join, check_o5)
 
 
 # -------------------------------------------------------------- the pins
@@ -167,6 +261,35 @@ def test_join_golden():
 
 def test_str_golden():
     check_str_golden(oracle.load())
+
+
+def test_sorted_children_build():
+    check_sorted_build(oracle.load())
+
+
+def test_sorted_children_entries_ascend():
+    rects = random_case("clustered", 4000, 12)
+    e = oracle.Tree(rects, None, 16, sort_children=True).export()
+    for g, c in enumerate(e["counts"]):
+        assert np.all(np.diff(e["mbrs"][g, :c, 0]) >= 0)
+
+
+def test_pruned_join_matches_brute():
+    check_pruned_join(oracle.load())
+
+
+def test_o5_worked_example_and_brute_force():
+    check_o5(oracle.load())
+
+
+def test_pruned_join_saves_tests_on_workload_shapes():
+    j = dg.workload("join", n=20000)
+    a = oracle.Tree(j.rects, j.ids, 32, sort_children=True)
+    b = oracle.Tree(j.rects_s, j.ids_s, 32, sort_children=True)
+    got, tests = a.join_pruned(b)
+    assert np.array_equal(got, oracle.Tree(j.rects, j.ids, 32).join(oracle.Tree(j.rects_s, j.ids_s, 32)))
+    plain = oracle.Tree(j.rects, j.ids, 32).join_tests(oracle.Tree(j.rects_s, j.ids_s, 32))
+    assert tests < plain
 
 
 @pytest.mark.parametrize("kind", ["uniform", "clustered", "grid", "points", "dups", "negative"])
@@ -329,6 +452,15 @@ MUTANTS = [
     ("STR centre key", "float k = lo + hi;", "float k = lo;"),
     ("STR tie order", "return (a->idx > b->idx) - (a->idx < b->idx);", "return (a->idx < b->idx) - (a->idx > b->idx);"),
     ("leaf packing off by one", "int64_t lo = k * fanout, hi", "int64_t lo = k * fanout + (k > 0), hi"),
+    ("child sort unstable on ties", "while (k >= 0 && nd->mbr[k].lx > b.lx)",
+     "while (k >= 0 && nd->mbr[k].lx >= b.lx)"),
+    ("child sort moves MBRs only", "nd->child[k + 1] = nd->child[k];", "nd->child[k + 1] = nd->child[k + 1];"),
+    ("O3 on the wrong key", "if (a->mbr[i].lx <= b->mbr[j].hx)", "if (a->mbr[i].hx <= b->mbr[j].lx)"),
+    ("O4 drops touching pairs", "if (b->mbr[j].lx > a->mbr[i].hx) /* O4 */",
+     "if (b->mbr[j].lx >= a->mbr[i].hx) /* O4 */"),
+    ("O5 moves the wrong way", "g[i] = pass ? g[i] + step : g[i] - step;",
+     "g[i] = pass ? g[i] - step : g[i] + step;"),
+    ("O5 one round short", "int rounds = logp + 1;", "int rounds = logp;"),
 ]
 
 
