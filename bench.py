@@ -375,29 +375,47 @@ def run_ours(args):
         jr = torch.from_numpy(j.rects).to(dev)
         js = torch.from_numpy(j.rects_s).to(dev)
 
-        def jstep():
-            a = rt.RTree(jr, None, fanout=32, stream=stream)
-            b = rt.RTree(js, None, fanout=32, stream=stream)
-            r = a.join(b, stream=stream)
+        def jstep(sort_children=False, prune="off"):
+            a = rt.RTree(jr, None, fanout=32, stream=stream, sort_children=sort_children)
+            b = rt.RTree(js, None, fanout=32, stream=stream, sort_children=sort_children)
+            r = a.join(b, stream=stream, prune=prune)
             tot = r.total
             r.close(); a.close(); b.close()
             return tot
 
-        pairs = jstep()
-        jstep()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        kj = max(1, args.steps)
-        e0.record(stream)
-        for _ in range(kj):
-            jstep()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        jms = max_over_ranks(e0.elapsed_time(e1) / kj, world, dev)
+        def jtime(**kw):
+            pairs = jstep(**kw)
+            jstep(**kw)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            kj = max(1, args.steps)
+            e0.record(stream)
+            for _ in range(kj):
+                jstep(**kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1) / kj, world, dev)
+            # kernel breakdown from a separate, instrumented step
+            rt.rtree_timing_reset()
+            rt.rtree_timing_enable(True)
+            jstep(**kw)
+            torch.cuda.synchronize()
+            rt.rtree_timing_enable(False)
+            k = rt.rtree_timing_get()
+            trav = sum(v[1] for n, v in k.items() if n.startswith("join_"))
+            return pairs, ms, trav
+
+        pairs, jms, jtrav = jtime()
+        ppairs, pms, ptrav = jtime(sort_children=True, prune="on")
+        assert ppairs == pairs
         join = {"metric": "join pairs/s (2M x 2M, build of both trees included)",
                 "value": round(pairs * world / (jms / 1e3), 1), "unit": "pairs/s",
-                "pairs": int(pairs), "ms_per_step": round(jms, 3)}
+                "pairs": int(pairs), "ms_per_step": round(jms, 3),
+                "traversal_ms": round(jtrav, 3),
+                "pruned": {"what": "sorted-children trees, O3 + O4/O5 pruned join (Section 4.2)",
+                           "value": round(ppairs * world / (pms / 1e3), 1), "unit": "pairs/s",
+                           "ms_per_step": round(pms, 3), "traversal_ms": round(ptrav, 3)}}
 
     # ---- CPU oracle baseline (rank 0, one GPU runs only)
     cpu = None

@@ -73,9 +73,12 @@ enum {
 
 /* Build configuration.  A zeroed struct (or NULL) selects the defaults. */
 typedef struct rtree_config {
-    int32_t fanout; /* maximum entries per node F: 4, 8, 16, 32, 64 or 128; 0 -> 16 */
-    int32_t layout; /* RTREE_LAYOUT_*; default SOA */
-    int32_t reserved[6];
+    int32_t fanout;        /* maximum entries per node F: 4, 8, 16, 32, 64 or 128; 0 -> 16 */
+    int32_t layout;        /* RTREE_LAYOUT_*; default SOA */
+    int32_t sort_children; /* 1: every node's entries ascend by xmin, ties in packing order
+                              (the node order the join prunings of Section 4.2 assume);
+                              0 (default): packing order */
+    int32_t reserved[5];
 } rtree_config_t;
 
 /* Range-select options.  NULL selects the defaults. */
@@ -97,6 +100,8 @@ typedef struct rtree_info {
     int32_t device;       /* CUDA device holding the tree */
     int64_t device_bytes; /* device memory held by the tree */
     float root_mbr[4];    /* bounding box of all rectangles (empty tree: +inf,+inf,-inf,-inf) */
+    int32_t sort_children; /* as built (rtree_config_t) */
+    int32_t reserved[3];
 } rtree_info_t;
 
 /*
@@ -109,7 +114,10 @@ typedef struct rtree_info {
  * into S = ceil(sqrt(ceil(m/F))) slabs of S*F items, each slab sorted by
  * ymin+ymax (ties by item index), and runs of F items become nodes; this is
  * repeated on the node MBRs until one node (the root) remains.  A centre key
- * that is NaN (-inf + inf) counts as 0 and -0 as +0.
+ * that is NaN (-inf + inf) counts as 0 and -0 as +0.  With
+ * cfg->sort_children the entries of every node are then reordered by
+ * ascending xmin (stable; -0 equals +0), which changes neither the nodes'
+ * contents nor any query result.
  *
  * rects: n*4 floats, ids: n int32 (NULL -> ids 0..n-1); host or device.
  * n = 0 builds a valid empty tree.  n must be < 2^31.
@@ -324,6 +332,36 @@ RTREE_API rtree_status rtree_range_select_stats(const rtree_t *tree, const float
  * same device.  Errors: RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA.
  */
 RTREE_API rtree_status rtree_join(const rtree_t *r, const rtree_t *s, void *stream, rtree_result_t **out);
+
+/*
+ * rtree_join_ex -- rtree_join with options: the sorted-node prunings of
+ * Section 4.2 for trees built with sort_children.
+ *
+ * On equal-height node pairs the outer node's children are taken 32 at a
+ * time, one per lane, in ascending xmin.  O3: an outer child whose xmin lies
+ * right of every inner child (right of the inner node's MBR) fails for all
+ * of them, and so does every later outer child, so the rest of the outer
+ * node is skipped; an outer child that misses the inner node's MBR is also
+ * not paired (the search-space restriction of Brinkhoff, Kriegel and Seeger
+ * 1993).  O4/O5: each remaining outer child finds, with the batched search
+ * of the many-to-many comparison (log2(P)+1 rounds over the inner children's
+ * xmin, P = inner count rounded up to a power of two), the number f of inner
+ * children that start left of its xmax; only those f are tested, the pairs
+ * of all 32 lanes packed densely onto the warp.  The result is identical to
+ * rtree_join's.
+ *
+ * opts NULL -> RTREE_PRUNE_AUTO.  Errors: as rtree_join, and RTREE_EINVAL
+ * for RTREE_PRUNE_ON when either tree was built without sort_children.
+ */
+enum { RTREE_PRUNE_AUTO = 0, /* prune when both trees have sorted children */
+       RTREE_PRUNE_OFF = 1,  /* plain one-to-many comparison */
+       RTREE_PRUNE_ON = 2 };
+typedef struct rtree_join_opts {
+    int32_t prune; /* RTREE_PRUNE_* */
+    int32_t reserved[7];
+} rtree_join_opts_t;
+RTREE_API rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s, const rtree_join_opts_t *opts,
+                                     void *stream, rtree_result_t **out);
 
 /* Result accessors.  Pointers are device pointers owned by the result. */
 RTREE_API int64_t rtree_result_total(const rtree_result_t *res);         /* ids (select) or pairs (join) */

@@ -12,6 +12,10 @@
 //   node k = items B[kF .. kF+F), only the last node of a level may be partial.
 // A centre key of NaN (-inf + inf) counts as 0 and -0 as +0.
 //
+// With sort_children, the items of each packed node are then reordered by
+// ascending lx (ties keep their packing position), the node order Section
+// 4.2 assumes for its join prunings.  Which items share a node is unchanged.
+//
 // The nodes are then laid out level by level from the root; a level's nodes
 // appear in the order their parents list them, so every node's children are
 // contiguous and every subtree owns a contiguous run of leaf entries.  Only
@@ -106,6 +110,57 @@ __global__ void k_node_boxes(const float4 *__restrict__ items, const uint32_t *_
             acc.w = fmaxf(acc.w, b.w);
         }
         out[k] = acc;
+    }
+}
+
+// One warp per packed node: ranks each item by (lx, packing position) among
+// the node's items and rewrites the node's run of pack[] in that order.
+__global__ void k_sort_children(const float4 *__restrict__ items, uint32_t *__restrict__ pack,
+                                int64_t m, int F, int64_t P)
+{
+    constexpr int kMaxPer = 4;  // F <= 128
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int per = (F + 31) / 32;
+    for (int64_t k = warp; k < P; k += nwarps) {
+        const int64_t lo = k * F;
+        const int cnt = (int)(m - lo < F ? m - lo : F);
+        uint32_t it[kMaxPer];
+        float lx[kMaxPer];
+#pragma unroll
+        for (int t = 0; t < kMaxPer; ++t) {
+            const int j = t * 32 + lane;
+            it[t] = 0xffffffffu;
+            lx[t] = __int_as_float(0x7f800000);  // +inf: never ranks below a real item
+            if (t < per && j < cnt) {
+                it[t] = pack[lo + j];
+                if (it[t] < (uint64_t)m)
+                    lx[t] = items[it[t]].x;
+            }
+        }
+        int rank[kMaxPer] = {0, 0, 0, 0};
+        for (int t2 = 0; t2 < per; ++t2) {
+            for (int src = 0; src < 32; ++src) {
+                const float v = __shfl_sync(RT_FULL, lx[t2], src);
+                const int jv = t2 * 32 + src;
+                if (jv >= cnt)
+                    break;  // uniform: jv depends only on the loop counters
+#pragma unroll
+                for (int t = 0; t < kMaxPer; ++t) {
+                    const int j = t * 32 + lane;
+                    rank[t] += (v < lx[t]) || (v == lx[t] && jv < j);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kMaxPer; ++t) {
+            const int j = t * 32 + lane;
+            if (t < per && j < cnt && rank[t] < cnt)
+                pack[lo + rank[t]] = it[t];
+        }
+        __syncwarp();
     }
 }
 
@@ -209,10 +264,11 @@ int bits_for(uint64_t v)  // bits needed to hold values 0..v
 }  // namespace
 
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int F, int layout,
-                        cudaStream_t s, rtree *t)
+                        bool sort_children, cudaStream_t s, rtree *t)
 {
     t->fanout = F;
     t->layout = layout;
+    t->sorted = sort_children ? 1 : 0;
     t->n = n;
     t->levels = 0;
     t->nodes = 0;
@@ -310,6 +366,11 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
                     RT_LAUNCH();
                 }
                 RT_TRY(radix_sort_pairs(k0.p, v0.p, k1.p, pack->p, m, 0, 32, s));
+            }
+            if (sort_children && F > 1) {
+                KernelTimer kt_("sort_children", s);
+                k_sort_children<<<blocks_for(P * 32), kThreads, 0, s>>>(cur, pack->p, m, F, P);
+                RT_LAUNCH();
             }
             auto *nb = new DevBuf<float4>(s);
             boxes.push_back(nb);

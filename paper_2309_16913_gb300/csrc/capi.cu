@@ -188,6 +188,9 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
         return fail(RTREE_EINVAL, "rtree_build: rects is NULL");
     const int F = (cfg && cfg->fanout) ? cfg->fanout : 16;
     const int layout = cfg ? cfg->layout : RTREE_LAYOUT_SOA;
+    const bool sort_children = cfg && cfg->sort_children;
+    if (cfg && cfg->sort_children != 0 && cfg->sort_children != 1)
+        return fail(RTREE_EINVAL, "rtree_build: sort_children must be 0 or 1");
     if (!fanout_ok(F))
         return fail(RTREE_EINVAL, "rtree_build: fanout %d not in {4,8,16,32,64,128}", F);
     if (layout != RTREE_LAYOUT_SOA && layout != RTREE_LAYOUT_AOS)
@@ -212,7 +215,7 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
             if (st == RTREE_OK && ids)
                 st = stage<int32_t>(ids, (size_t)n * 4, 4, s, itmp, &dids);
             if (st == RTREE_OK)
-                st = build_tree(drects, dids, n, F, layout, s, t);
+                st = build_tree(drects, dids, n, F, layout, sort_children, s, t);
             if (st == RTREE_OK) {
                 cudaError_t e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess)
@@ -256,6 +259,8 @@ rtree_status rtree_get_info(const rtree_t *t, rtree_info_t *info)
     info->device = t->device;
     info->device_bytes = t->bytes;
     memcpy(info->root_mbr, t->root_mbr, sizeof(info->root_mbr));
+    info->sort_children = t->sorted;
+    memset(info->reserved, 0, sizeof(info->reserved));
     return RTREE_OK;
 }
 
@@ -391,6 +396,12 @@ rtree_status rtree_range_select_stats(const rtree_t *t, const float *queries, in
 
 rtree_status rtree_join(const rtree_t *r, const rtree_t *s_tree, void *stream, rtree_result_t **out)
 {
+    return rtree_join_ex(r, s_tree, nullptr, stream, out);
+}
+
+rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s_tree, const rtree_join_opts_t *opts,
+                           void *stream, rtree_result_t **out)
+{
     clear_error();
     if (!out)
         return fail(RTREE_EINVAL, "rtree_join: out is NULL");
@@ -399,12 +410,18 @@ rtree_status rtree_join(const rtree_t *r, const rtree_t *s_tree, void *stream, r
         return fail(RTREE_EINVAL, "rtree_join: tree is NULL");
     if (r->device != s_tree->device)
         return fail(RTREE_EINVAL, "rtree_join: trees on devices %d and %d", r->device, s_tree->device);
+    const int prune = opts ? opts->prune : RTREE_PRUNE_AUTO;
+    if (prune != RTREE_PRUNE_AUTO && prune != RTREE_PRUNE_OFF && prune != RTREE_PRUNE_ON)
+        return fail(RTREE_EINVAL, "rtree_join: unknown prune mode %d", prune);
+    const bool both_sorted = r->sorted && s_tree->sorted;
+    if (prune == RTREE_PRUNE_ON && !both_sorted)
+        return fail(RTREE_EINVAL, "rtree_join: pruning needs both trees built with sort_children");
     try {
         DeviceGuard guard(r->device);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         rtree_result *res = new rtree_result();
         res->device = r->device;
-        rtree_status st = tree_join(r, s_tree, s, res);
+        rtree_status st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res);
         if (st == RTREE_OK) {
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess)

@@ -114,6 +114,7 @@ struct TreeDev {
     int32_t levels;
     int32_t fanout;
     int32_t layout;
+    int32_t sorted;  // entries of every node ascend by lx
 };
 
 }  // namespace rt
@@ -122,6 +123,7 @@ struct rtree {
     int device = 0;
     int32_t fanout = 16;
     int32_t layout = RTREE_LAYOUT_SOA;
+    int32_t sorted = 0;  // built with sort_children
     int32_t levels = 0;
     int64_t n = 0;
     int64_t nodes = 0;
@@ -146,6 +148,7 @@ struct rtree {
         v.levels = levels;
         v.fanout = fanout;
         v.layout = layout;
+        v.sorted = sorted;
         return v;
     }
 };
@@ -291,9 +294,10 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *off, int64_t nse
 rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
                             cudaStream_t s);
 
-// Builds the tree from device rectangles (float4 rows) and device ids (or NULL).
+// Builds the tree from device rectangles (float4 rows) and device ids (or
+// NULL); sort_children orders every node's entries by ascending lx.
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int fanout, int layout,
-                        cudaStream_t s, rtree *t);
+                        bool sort_children, cudaStream_t s, rtree *t);
 
 // Range select for device queries (float4 rows).
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,
@@ -310,7 +314,9 @@ rtree_status select_pass(const rtree *t, const float4 *queries, int64_t q, int32
 rtree_status select_stats(const rtree *t, const float4 *queries, int64_t q, cudaStream_t s,
                           int64_t out[8]);
 
-// R-tree join of two trees on the same device.
-rtree_status tree_join(const rtree *r, const rtree *s_tree, cudaStream_t s, rtree_result *res);
+// R-tree join of two trees on the same device; prune selects the sorted-node
+// kernel for equal-height pairs (both trees must have sorted children).
+rtree_status tree_join(const rtree *r, const rtree *s_tree, bool prune, cudaStream_t s,
+                       rtree_result *res);
 
 }  // namespace rt

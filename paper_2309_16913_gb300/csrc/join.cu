@@ -12,6 +12,15 @@
 // Where the heights differ, only the taller tree descends: its children are
 // tested against the other node's bounding box.
 //
+// For trees whose node entries ascend by lx, equal-height pairs can use the
+// prunings of Section 4.2 instead (k_join_pruned): O3 ends the outer loop at
+// the first outer child whose lx lies right of every inner child, and O4/O5
+// bound each outer child's inner scan by the number f of inner children that
+// start left of its hx, found by the batched search of the many-to-many
+// comparison.  The f candidate pairs of all lanes are then packed densely
+// onto the warp, so a node pair costs ceil(sum f / 32) tests instead of one
+// per outer child.
+//
 // Output is written in two passes per level (count, scan, scatter).  The
 // final (r_id, s_id) pairs are sorted lexicographically by two stable radix
 // sorts (by s, then by r).
@@ -94,11 +103,123 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+constexpr int kMaxFanout = 128;
+
+__device__ __forceinline__ float entry_lx(const TreeDev &t, int64_t g, int j)
+{
+    if (t.layout == RTREE_LAYOUT_AOS)
+        return __ldg(reinterpret_cast<const float *>(t.mbr) + (g * t.fanout + j) * 4);
+    return __ldg(t.mbr + g * 4 * t.fanout + j);
+}
+
+// Equal-height node pairs of two sorted-children trees, one pair per warp.
+template <bool LEAF, int PASS>
+__global__ void __launch_bounds__(kThreads)
+    k_join_pruned(TreeDev ta, TreeDev tb, const int2 *__restrict__ pairs, int64_t np,
+                  int32_t *__restrict__ counts, const int64_t *__restrict__ offs,
+                  int2 *__restrict__ out)
+{
+    __shared__ float s_lx[kThreads / 32][kMaxFanout];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    float *lxs = s_lx[threadIdx.x >> 5];
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < np; p += nwarps) {
+        const int2 pr = pairs[p];
+        const int a = pr.x, b = pr.y;
+        const int4 ma = __ldg(ta.meta + a), mb = __ldg(tb.meta + b);
+        const float4 bb = __ldg(tb.nbox + b);  // inner node MBR: max over children of hx is bb.z
+        const int nin = mb.y;
+        int64_t base = 0;
+        if (PASS == PASS_SCATTER)
+            base = offs[p];
+        __syncwarp();  // the previous pair's searches are done with lxs
+        for (int j = lane; j < nin; j += 32)
+            lxs[j] = entry_lx(tb, b, j);
+        __syncwarp();
+        int P2 = 1, rounds = 1;  // inner count rounded up to a power of two; log2(P2)+1 rounds
+        while (P2 < nin) {
+            P2 <<= 1;
+            ++rounds;
+        }
+        int cur = 0;
+        for (int i0 = 0; i0 < ma.y; i0 += 32) {
+            const int i = i0 + lane;
+            const bool vi = i < ma.y;
+            const float4 ob = vi ? load_entry(ta.mbr, ta.layout, ta.fanout, a, i) : empty_box();
+            const bool keyok = vi && ob.x <= bb.z;   // O3 key test against all inner children
+            const bool cand = keyok && meets(ob, bb);  // search-space restriction
+            int f = 0;
+            if (cand) {  // O5: first inner index whose lx exceeds ob.hx
+                int g = P2 >> 1, step = (P2 >> 2) > 1 ? (P2 >> 2) : 1;
+                f = nin;
+                for (int r = 0; r < rounds; ++r) {
+                    const bool pass = g < nin && ob.z >= lxs[g];
+                    if (!pass && g < f)
+                        f = g;
+                    g = pass ? g + step : g - step;
+                    step = (step >> 1) > 1 ? (step >> 1) : 1;
+                }
+            }
+            int incl = f;  // inclusive scan of the bounds over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(RT_FULL, incl, o);
+                if (lane >= o)
+                    incl += u;
+            }
+            const int excl = incl - f;
+            const int T = __shfl_sync(RT_FULL, incl, 31);
+            for (int k0 = 0; k0 < T; k0 += 32) {
+                const int k = k0 + lane;
+                int own = 0;  // the lane whose run [excl, incl) holds k
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int v = __shfl_sync(RT_FULL, incl, own + st - 1);
+                    if (v <= k)
+                        own += st;
+                }
+                const int ex = __shfl_sync(RT_FULL, excl, own);
+                const float4 o = make_float4(__shfl_sync(RT_FULL, ob.x, own),
+                                             __shfl_sync(RT_FULL, ob.y, own),
+                                             __shfl_sync(RT_FULL, ob.z, own),
+                                             __shfl_sync(RT_FULL, ob.w, own));
+                const int j = k - ex;
+                bool hit = false;
+                if (k < T)
+                    hit = meets(o, load_entry(tb.mbr, tb.layout, tb.fanout, b, j));
+                const unsigned m = __ballot_sync(RT_FULL, hit);
+                if (PASS == PASS_SCATTER && hit) {
+                    const int io = i0 + own;
+                    int2 v;
+                    if (LEAF)
+                        v = make_int2(__ldg(ta.ids + ma.x + io), __ldg(tb.ids + mb.x + j));
+                    else
+                        v = make_int2(ma.x + io, mb.x + j);
+                    out[base + cur + __popc(m & lt)] = v;
+                }
+                cur += __popc(m);
+            }
+            // O3: outer children ascend by lx, so after one fails the key test
+            // every later one fails it too
+            if (__ballot_sync(RT_FULL, vi && !keyok) != 0)
+                break;
+        }
+        if (PASS == PASS_COUNT && lane == 0)
+            counts[p] = cur;
+    }
+}
+
 using JoinKernel = void (*)(TreeDev, TreeDev, const int2 *, int64_t, int32_t *, const int64_t *,
                             int2 *);
 
-JoinKernel pick(int mode, int pass)
+JoinKernel pick(int mode, int pass, bool prune)
 {
+    if (prune && mode == J_BOTH)
+        return pass == PASS_COUNT ? k_join_pruned<false, PASS_COUNT> : k_join_pruned<false, PASS_SCATTER>;
+    if (prune && mode == J_LEAF)
+        return pass == PASS_COUNT ? k_join_pruned<true, PASS_COUNT> : k_join_pruned<true, PASS_SCATTER>;
     switch (mode) {
     case J_BOTH: return pass == PASS_COUNT ? k_join<J_BOTH, PASS_COUNT> : k_join<J_BOTH, PASS_SCATTER>;
     case J_A: return pass == PASS_COUNT ? k_join<J_A, PASS_COUNT> : k_join<J_A, PASS_SCATTER>;
@@ -180,7 +301,8 @@ rtree_status sort_pairs(int2 *pairs, int64_t n, cudaStream_t s)
 
 }  // namespace
 
-rtree_status tree_join(const rtree *R, const rtree *S, cudaStream_t s, rtree_result *res)
+rtree_status tree_join(const rtree *R, const rtree *S, bool prune, cudaStream_t s,
+                       rtree_result *res)
 {
     res->rows = 0;
     res->total = 0;
@@ -207,8 +329,8 @@ rtree_status tree_join(const rtree *R, const rtree *S, cudaStream_t s, rtree_res
         RT_TRY(cnt.alloc(np, "join counts"));
         RT_TRY(off.alloc(np + 1, "join offsets"));
         {
-            KernelTimer kt_("join_count", s);
-            pick(mode, PASS_COUNT)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np, cnt.p,
+            KernelTimer kt_(prune ? "join_pruned_count" : "join_count", s);
+            pick(mode, PASS_COUNT, prune)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np, cnt.p,
                                                                      nullptr, nullptr);
             RT_LAUNCH();
         }
@@ -219,8 +341,8 @@ rtree_status tree_join(const rtree *R, const rtree *S, cudaStream_t s, rtree_res
         DevBuf<int2> next(s);
         RT_TRY(next.alloc(total, mode == J_LEAF ? "join pairs" : "join frontier"));
         if (total > 0) {
-            KernelTimer kt_("join_scatter", s);
-            pick(mode, PASS_SCATTER)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np,
+            KernelTimer kt_(prune ? "join_pruned_scatter" : "join_scatter", s);
+            pick(mode, PASS_SCATTER, prune)<<<grid_for(np), kThreads, 0, s>>>(ta, tb, front.p, np,
                                                                        nullptr, off.p, next.p);
             RT_LAUNCH();
         }

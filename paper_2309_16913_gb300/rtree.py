@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_E
                 4: "RTREE_ETIMEOUT", 5: "RTREE_EOVERFLOW", 6: "RTREE_EINTERNAL"}
 LAYOUTS = {"soa": 0, "aos": 1}
 MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
+PRUNES = {"auto": 0, "off": 1, "on": 2}
 
 
 class RTreeError(RuntimeError):
@@ -37,7 +38,12 @@ class RTreeError(RuntimeError):
 
 
 class rtree_config_t(C.Structure):
-    _fields_ = [("fanout", C.c_int32), ("layout", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("fanout", C.c_int32), ("layout", C.c_int32), ("sort_children", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class rtree_join_opts_t(C.Structure):
+    _fields_ = [("prune", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class rtree_select_opts_t(C.Structure):
@@ -76,7 +82,8 @@ class rtree_tune_result_t(C.Structure):
 class rtree_info_t(C.Structure):
     _fields_ = [("n", C.c_int64), ("nodes", C.c_int64), ("levels", C.c_int32),
                 ("fanout", C.c_int32), ("layout", C.c_int32), ("device", C.c_int32),
-                ("device_bytes", C.c_int64), ("root_mbr", C.c_float * 4)]
+                ("device_bytes", C.c_int64), ("root_mbr", C.c_float * 4),
+                ("sort_children", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _lock = threading.Lock()
@@ -92,6 +99,7 @@ def _bind(lib):
         "rtree_export": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
         "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
+        "rtree_join_ex": (C.c_int, [vp, vp, vp, vp, C.POINTER(vp)]),
         "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
         "rtree_range_select_noalloc": (C.c_int, [vp, vp, i64, vp, vp, i64, C.POINTER(C.c_int64), vp]),
         "rtree_result_total": (i64, [vp]),
@@ -206,7 +214,8 @@ def _stream(stream) -> int:
 
 
 # ------------------------------------------------- C names, thin wrappers
-def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None) -> int:
+def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None,
+                sort_children: bool = False) -> int:
     """Builds a tree; returns the opaque handle (free with rtree_free)."""
     lib = load_library()
     rp, n, keep_r = _as_rows(rects, "rects")
@@ -214,6 +223,7 @@ def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", st
     cfg = rtree_config_t()
     cfg.fanout = int(fanout)
     cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    cfg.sort_children = 1 if sort_children else 0
     out = C.c_void_p()
     _check(lib.rtree_build(rp, ip, n, C.byref(cfg), _stream(stream), C.byref(out)), lib)
     del keep_r, keep_i
@@ -231,7 +241,8 @@ def rtree_get_info(handle: int) -> dict:
     _check(lib.rtree_get_info(handle, C.byref(info)), lib)
     return {"n": info.n, "nodes": info.nodes, "levels": info.levels, "fanout": info.fanout,
             "layout": info.layout, "device": info.device, "device_bytes": info.device_bytes,
-            "root_mbr": np.array(info.root_mbr[:], dtype=np.float32)}
+            "root_mbr": np.array(info.root_mbr[:], dtype=np.float32),
+            "sort_children": info.sort_children}
 
 
 def rtree_export(handle: int, stream=None) -> dict:
@@ -294,6 +305,16 @@ def rtree_join(r_handle: int, s_handle: int, stream=None) -> int:
     lib = load_library()
     out = C.c_void_p()
     _check(lib.rtree_join(r_handle, s_handle, _stream(stream), C.byref(out)), lib)
+    return out.value
+
+
+def rtree_join_ex(r_handle: int, s_handle: int, prune: str | int = "auto", stream=None) -> int:
+    """rtree_join with the sorted-node prunings ("auto", "off" or "on")."""
+    lib = load_library()
+    opts = rtree_join_opts_t()
+    opts.prune = PRUNES[prune] if isinstance(prune, str) else int(prune)
+    out = C.c_void_p()
+    _check(lib.rtree_join_ex(r_handle, s_handle, C.byref(opts), _stream(stream), C.byref(out)), lib)
     return out.value
 
 
@@ -598,9 +619,10 @@ class Server:
 class RTree:
     """An R-tree on the GPU: build, range select, join."""
 
-    def __init__(self, rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None):
+    def __init__(self, rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None,
+                 sort_children: bool = False):
         self.handle = None
-        self.handle = rtree_build(rects, ids, fanout, layout, stream)
+        self.handle = rtree_build(rects, ids, fanout, layout, stream, sort_children)
 
     def __del__(self):
         self.close()
@@ -628,5 +650,7 @@ class RTree:
     def select_stats(self, queries, stream=None) -> dict:
         return rtree_range_select_stats(self.handle, queries, stream)
 
-    def join(self, other: "RTree", stream=None) -> Result:
-        return Result(rtree_join(self.handle, other.handle, stream))
+    def join(self, other: "RTree", stream=None, prune: str | int | None = None) -> Result:
+        if prune is None:
+            return Result(rtree_join(self.handle, other.handle, stream))
+        return Result(rtree_join_ex(self.handle, other.handle, prune, stream))

@@ -56,7 +56,9 @@ def test_struct_layouts_match_header(tmp_path):
                    " sizeof(rtree_select_opts_t), sizeof(rtree_info_t), offsetof(rtree_info_t, device_bytes),"
                    " offsetof(rtree_info_t, root_mbr), sizeof(rtree_server_config_t),"
                    " offsetof(rtree_server_config_t, max_batch_ids), sizeof(rtree_reply_t),"
-                   " offsetof(rtree_reply_t, latency_us), sizeof(rtree_server_stats_t)); return 0;}\n")
+                   " offsetof(rtree_reply_t, latency_us), sizeof(rtree_server_stats_t)); "
+                   "printf(\"%zu %zu %zu %zu\\n\", offsetof(rtree_config_t, sort_children), sizeof(rtree_join_opts_t),"
+                   " offsetof(rtree_info_t, sort_children), (size_t)RTREE_PRUNE_ON); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
@@ -64,7 +66,8 @@ def test_struct_layouts_match_header(tmp_path):
             rt.rtree_info_t.device_bytes.offset, rt.rtree_info_t.root_mbr.offset,
             C.sizeof(rt.rtree_server_config_t), rt.rtree_server_config_t.max_batch_ids.offset,
             C.sizeof(rt.rtree_reply_t), rt.rtree_reply_t.latency_us.offset,
-            C.sizeof(rt.rtree_server_stats_t)]
+            C.sizeof(rt.rtree_server_stats_t), rt.rtree_config_t.sort_children.offset,
+            C.sizeof(rt.rtree_join_opts_t), rt.rtree_info_t.sort_children.offset, rt.PRUNES["on"]]
     assert got == want
 
 
@@ -81,6 +84,11 @@ def test_argument_errors_need_no_gpu(lib):
     assert b"fanout" in lib.rtree_last_error()
     assert lib.rtree_range_select(None, None, 0, None, None, C.byref(out)) == rt.RTREE_EINVAL
     assert lib.rtree_join(None, None, None, C.byref(out)) == rt.RTREE_EINVAL
+    assert lib.rtree_join_ex(None, None, None, None, C.byref(out)) == rt.RTREE_EINVAL
+    cfg = rt.rtree_config_t()
+    cfg.sort_children = 2
+    assert lib.rtree_build(None, None, 0, C.byref(cfg), None, C.byref(out)) == rt.RTREE_EINVAL
+    assert b"sort_children" in lib.rtree_last_error()
     assert lib.rtree_result_total(None) == 0
     lib.rtree_free(None)
     lib.rtree_result_free(None)
