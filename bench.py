@@ -57,6 +57,9 @@ def parse_args():
                          "with the full-size hit-count mix)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-join", action="store_true")
+    ap.add_argument("--no-order", action="store_true")
+    ap.add_argument("--order", choices=["auto", "input", "hilbert"], default="auto",
+                    help="traversal order of the query batch (auto: the autotuner picks)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -246,30 +249,32 @@ def run_ours(args):
     queries = torch.from_numpy(w.queries).to(dev)
     torch.cuda.synchronize()
 
-    def step(F, layout, mapping):
+    def step(F, layout, mapping, order="input"):
         t = rt.RTree(rects, ids, fanout=F, layout=layout, stream=stream)
-        res = t.range_select(queries, mapping=mapping, stream=stream)
+        res = t.range_select(queries, mapping=mapping, stream=stream, order=order)
         total = res.total
         res.close()
         t.close()
         return total
 
-    # ---- pick fanout/layout by timing one step each (untimed for the result)
-    # pick fanout / layout / mapping with the library's autotuner (one
-    # build + sorted select per configuration, CUDA-event timed)
+    # ---- pick fanout / layout / mapping / traversal order with the library's
+    # autotuner (one build + sorted select per configuration, CUDA-event timed)
     fanouts = [args.fanout] if args.fanout else [16, 32, 64]
-    tune = rt.rtree_autotune(rects, queries, ids, fanouts=fanouts, include_build=True, stream=stream)
+    tune = rt.rtree_autotune(rects, queries, ids, fanouts=fanouts, include_build=True, stream=stream,
+                             orders=args.order != "input")
     sweep = {k: v for k, v in tune["all"].items()
              if (args.layout == "auto" or f"_{args.layout}_" in k)
-             and (args.mapping == "auto" or k.endswith(args.mapping))}
+             and (args.mapping == "auto" or args.mapping in k)
+             and (args.order == "auto" or k.endswith("_hilbert") == (args.order == "hilbert"))}
     best = min(sweep, key=sweep.get)
     F = int(best.split("_")[0][1:])
     layout = best.split("_")[1]
-    mapping = best.split("_", 2)[2]
-    total_hits = step(F, layout, mapping)
+    order = "hilbert" if best.endswith("_hilbert") else "input"
+    mapping = best[len(f"F{F}_{layout}_"):].replace("_hilbert", "")
+    total_hits = step(F, layout, mapping, order)
 
     for _ in range(args.warmup):
-        step(F, layout, mapping)
+        step(F, layout, mapping, order)
     torch.cuda.synchronize()
 
     # ---- timed region
@@ -284,7 +289,7 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(F, layout, mapping)
+        step(F, layout, mapping, order)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -296,12 +301,13 @@ def run_ours(args):
     ms_max = max_over_ranks(ms_total, world, dev)
     value = Q * args.steps * world / (ms_max / 1e3)
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel; query-order comparison on the same tree
     with rt.RTree(rects, ids, fanout=F, layout=layout) as t:
         stats = t.select_stats(queries)
         res = t.range_select(queries)
         seg = np.diff(res.offsets_tensor().cpu().numpy())
         res.close()
+        order_cmp = None if args.no_order else compare_orders(rt, torch, t, queries, stream, mapping)
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
     breakdown = {}
@@ -340,7 +346,7 @@ def run_ours(args):
 
         def e2e_step():
             h = rt.rtree_build(h_rects, h_ids, F, layout, stream)
-            r = rt.rtree_range_select(h, h_q, mapping=mapping, stream=stream)
+            r = rt.rtree_range_select(h, h_q, mapping=mapping, stream=stream, order=order)
             rc = lib.rtree_result_copy_to_host(r, h_off.data_ptr(), h_out.data_ptr(), sptr)
             assert rc == 0, rt.rtree_last_error()
             rt.rtree_result_free(r)
@@ -431,7 +437,7 @@ def run_ours(args):
             "config": {"workload": f"scaled range select: {N} rects (80% 64-cluster gaussian, "
                                    f"20% uniform, sides log-U[1e-5,1e-3]), {Q} queries "
                                    "(selectivity log-U[1e-6,1e-3]), STR build + sorted select per step",
-                       "fanout": F, "layout": layout, "mapping": mapping,
+                       "fanout": F, "layout": layout, "mapping": mapping, "order": order,
                        "ids_returned_per_step": int(total_hits),
                        "l2": "inputs larger than L2 (rects 160 MB, tree ~200 MB; no flush)",
                        "sweep_ms_per_step": sweep, "seed": seed},
@@ -442,6 +448,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "join": join,
+            "query_order": order_cmp,
             "uneven": uneven,
             "serve": serve,
             "select_stats": stats,
@@ -450,6 +457,32 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def compare_orders(rt, torch, tree, queries, stream, mapping, reps=3):
+    """Select time (no build) with the batch taken in input order and in
+    Hilbert order of the query centres; the results are identical."""
+    out = {}
+    for order in ("input", "hilbert"):
+        for _ in range(2):
+            tree.range_select(queries, mapping=mapping, stream=stream, order=order).close()
+        torch.cuda.synchronize()
+        rt.rtree_timing_reset()
+        rt.rtree_timing_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            tree.range_select(queries, mapping=mapping, stream=stream, order=order).close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rt.rtree_timing_enable(False)
+        k = rt.rtree_timing_get()
+        trav = sum(v[1] for n, v in k.items() if n.startswith("select_")) / reps
+        out[order] = {"ms_per_select": round(e0.elapsed_time(e1) / reps, 3),
+                      "traversal_ms": round(trav, 3)}
+    out["what"] = "1M-query select on the built tree, no build; traversal = select_count + select_desc"
+    return out
 
 
 def run_uneven(args, rt, dg, torch, dev, stream, rank, world, F, layout):

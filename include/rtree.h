@@ -82,10 +82,20 @@ typedef struct rtree_config {
 } rtree_config_t;
 
 /* Range-select options.  NULL selects the defaults. */
+/* Traversal order of a batch (results are identical either way). */
+enum {
+    RTREE_ORDER_INPUT = 0,   /* queries are taken in the order given */
+    RTREE_ORDER_HILBERT = 1  /* taken in Hilbert-curve order of their centres, so that warps
+                                running together visit nearby nodes (an addition: the paper
+                                has no such step; it carries the latency-hiding aim of its
+                                prefetching, O2 in Section 3, over to the L2 cache) */
+};
+
 typedef struct rtree_select_opts {
     int32_t unsorted; /* 0 (default): ids of each query ascending; 1: traversal order */
     int32_t mapping;  /* RTREE_MAP_* */
-    int32_t reserved[6];
+    int32_t order;    /* RTREE_ORDER_*; rtree_range_select only (plans take INPUT) */
+    int32_t reserved[5];
 } rtree_select_opts_t;
 
 typedef struct rtree rtree_t;               /* opaque; owns device memory */
@@ -390,19 +400,21 @@ RTREE_API const char *rtree_version(void);
  * (NULL or 0 -> {16, 32, 64}; at most 8) and both layouts, and times a
  * sorted rtree_range_select of the q queries under both mappings with CUDA
  * events on `stream` (one untimed run first).  flags & RTREE_TUNE_INCLUDE_BUILD
- * adds the build time to each configuration's time.  *out receives the
- * fastest configuration and every configuration's time (at most 32).  Inputs
+ * adds the build time to each configuration's time; flags & RTREE_TUNE_ORDERS
+ * also tries every configuration with RTREE_ORDER_HILBERT.  *out receives the
+ * fastest configuration and every configuration's time (at most 64).  Inputs
  * may be host or device memory; callers pass a representative sample.
  */
-enum { RTREE_TUNE_INCLUDE_BUILD = 1 };
+enum { RTREE_TUNE_INCLUDE_BUILD = 1, RTREE_TUNE_ORDERS = 2 };
 
 typedef struct rtree_tune_result {
-    int32_t fanout, layout, mapping, tried;
+    int32_t fanout, layout, mapping, order, tried, reserved;
     double ms;              /* time of the chosen configuration */
-    double ms_all[32];      /* every configuration tried, in order */
-    int32_t fanout_all[32];
-    int32_t layout_all[32];
-    int32_t mapping_all[32];
+    double ms_all[64];      /* every configuration tried, in order */
+    int32_t fanout_all[64];
+    int32_t layout_all[64];
+    int32_t mapping_all[64];
+    int32_t order_all[64];
 } rtree_tune_result_t;
 
 RTREE_API rtree_status rtree_autotune(const float *rects, const int32_t *ids, int64_t n,

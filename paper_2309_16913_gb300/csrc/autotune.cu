@@ -2,7 +2,8 @@
 //
 // For each candidate fanout and layout the tree is built from the caller's
 // rectangles and the caller's queries are selected (sorted) under each
-// thread mapping; every configuration is timed with CUDA events on the
+// thread mapping (and, on request, each traversal order); every
+// configuration is timed with CUDA events on the
 // caller's stream after one untimed run, optionally including the build.
 // The fastest configuration is returned with all the times.  (The select's
 // per-warp stack needs no tuning: its depth has an exact bound.)
@@ -27,6 +28,7 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
         n_fanouts = 3;
     }
     const bool with_build = (flags & RTREE_TUNE_INCLUDE_BUILD) != 0;
+    const int n_orders = (flags & RTREE_TUNE_ORDERS) ? 2 : 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -50,9 +52,12 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
                 break;
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&build_ms, e0, e1);
-            for (int mapping = RTREE_MAP_WARP_PER_QUERY; mapping <= RTREE_MAP_WORK_QUEUE; ++mapping) {
+            for (int combo = 0; combo < 2 * n_orders && st == RTREE_OK; ++combo) {
+                const int mapping = RTREE_MAP_WARP_PER_QUERY + combo % 2;
+                const int order = combo / 2 ? RTREE_ORDER_HILBERT : RTREE_ORDER_INPUT;
                 rtree_select_opts_t opts{};
                 opts.mapping = mapping;
+                opts.order = order;
                 float sel_ms = 0.f;
                 for (int rep = 0; rep < 2 && st == RTREE_OK; ++rep) {  // untimed, then timed
                     rtree_result_t *res = nullptr;
@@ -68,11 +73,12 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
                 if (st != RTREE_OK)
                     break;
                 const double ms = sel_ms + (with_build ? build_ms : 0.f);
-                if (k < 32) {
+                if (k < 64) {
                     out->ms_all[k] = ms;
                     out->fanout_all[k] = cfg.fanout;
                     out->layout_all[k] = layout;
                     out->mapping_all[k] = mapping;
+                    out->order_all[k] = order;
                 }
                 ++k;
                 if (ms < best) {
@@ -80,13 +86,14 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
                     out->fanout = cfg.fanout;
                     out->layout = layout;
                     out->mapping = mapping;
+                    out->order = order;
                     out->ms = ms;
                 }
             }
             rtree_free(tree);
         }
     }
-    out->tried = k < 32 ? k : 32;
+    out->tried = k < 64 ? k : 64;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;

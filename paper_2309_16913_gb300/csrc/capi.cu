@@ -339,6 +339,9 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
     const int mapping = opts ? opts->mapping : RTREE_MAP_AUTO;
     if (mapping < RTREE_MAP_AUTO || mapping > RTREE_MAP_WORK_QUEUE)
         return fail(RTREE_EINVAL, "rtree_range_select: unknown mapping %d", mapping);
+    const int order = opts ? opts->order : RTREE_ORDER_INPUT;
+    if (order != RTREE_ORDER_INPUT && order != RTREE_ORDER_HILBERT)
+        return fail(RTREE_EINVAL, "rtree_range_select: unknown order %d", order);
     try {
         DeviceGuard guard(t->device);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -350,7 +353,7 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
             const float4 *dq = nullptr;
             st = stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq);
             if (st == RTREE_OK)
-                st = range_select(t, dq, q, sorted, mapping, s, res);
+                st = range_select(t, dq, q, sorted, mapping, order, s, res);
             if (st == RTREE_OK) {
                 cudaError_t e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess)

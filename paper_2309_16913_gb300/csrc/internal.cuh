@@ -240,6 +240,9 @@ struct SelIO {
     int64_t out_cap;
     int64_t leaf_cap;
     int64_t rng_cap;
+    // Optional traversal order: work item k is query order[k] (a permutation
+    // of [0, Q)); results stay indexed by the query.
+    const uint32_t *order;
 };
 
 // Caller-owned buffers for a select enqueued without host synchronization
@@ -299,9 +302,14 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int fanout, int layout,
                         bool sort_children, cudaStream_t s, rtree *t);
 
-// Range select for device queries (float4 rows).
+// Range select for device queries (float4 rows); order is RTREE_ORDER_*.
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,
-                          int mapping, cudaStream_t s, rtree_result *res);
+                          int mapping, int order, cudaStream_t s, rtree_result *res);
+
+// order[0 .. Q) = the queries' indices in Hilbert-curve order of their centres
+// (scaled into the tree's bounding box); ties keep index order.
+rtree_status hilbert_order(const rtree *t, const float4 *queries, int64_t Q, uint32_t *order,
+                           cudaStream_t s);
 
 // One pass of the range-select kernel on caller-provided buffers: the count
 // pass when counts is non-null, else the scatter pass.  ctr (one zeroed

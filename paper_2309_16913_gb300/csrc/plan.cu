@@ -205,6 +205,8 @@ rtree_status rtree_plan_create(const rtree_t *tree, int64_t max_queries, int64_t
         return fail(RTREE_EINVAL, "rtree_plan_create: need a tree, 1 <= max_queries < 2^31, max_ids >= 1");
     if (opts && opts->unsorted)
         return fail(RTREE_EINVAL, "rtree_plan_create: plans produce sorted results only");
+    if (opts && opts->order != RTREE_ORDER_INPUT)
+        return fail(RTREE_EINVAL, "rtree_plan_create: plans take queries in input order");
     const int mapping = opts ? opts->mapping : RTREE_MAP_AUTO;
     if (mapping < RTREE_MAP_AUTO || mapping > RTREE_MAP_WORK_QUEUE)
         return fail(RTREE_EINVAL, "rtree_plan_create: unknown mapping %d", mapping);

@@ -233,6 +233,8 @@ __global__ void __launch_bounds__(kThreads)
         qi = __shfl_sync(RT_FULL, qi, 0);
         if (qi >= (unsigned long long)Q)
             break;
+        if (io.order)
+            qi = __ldg(io.order + qi);
         const float4 q = __ldg(queries + qi);
         const Seg sg = seg_of(io, PASS, (int64_t)qi);
         Walk wk{0, 0, 0, 0, 0, false};
@@ -430,11 +432,11 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 __global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap, int64_t Q,
-                          unsigned long long *__restrict__ ctl)
+                          unsigned long long *__restrict__ ctl, const uint32_t *__restrict__ order)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cap;
          i += (long long)gridDim.x * blockDim.x)
-        items[i] = i < Q ? pack_item((int)i, 0) : kEmpty;
+        items[i] = i < Q ? pack_item(order ? (int)order[i] : (int)i, 0) : kEmpty;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl[0] = 0;                        // head
         ctl[1] = (unsigned long long)Q;    // tail
@@ -583,7 +585,7 @@ rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, con
     {
         KernelTimer kt_("wq_init", s);
         int64_t b = (cap_items + 255) / 256;
-        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items_p, cap_items, Q, ctl_p);
+        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items_p, cap_items, Q, ctl_p, io.order);
         RT_LAUNCH();
     }
     WorkQueue wq{items_p, cap_items, ctl_p, ctl_p + 1, reinterpret_cast<long long *>(ctl_p + 2)};
@@ -622,7 +624,7 @@ rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree
 }  // namespace
 
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
-                          int mapping, cudaStream_t s, rtree_result *res)
+                          int mapping, int order, cudaStream_t s, rtree_result *res)
 {
     const bool wq = mapping == RTREE_MAP_WORK_QUEUE;
     res->rows = Q;
@@ -641,8 +643,14 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     RT_TRY(ctr.alloc(2, "select work counters"));
     RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
     RT_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
+    DevBuf<uint32_t> perm(s);
+    if (order == RTREE_ORDER_HILBERT) {
+        RT_TRY(perm.alloc(Q, "query order"));
+        RT_TRY(hilbert_order(t, queries, Q, perm.p, s));
+    }
     SelIO io = unlimited();
     io.counts = cnt.p;
+    io.order = perm.p;
     if (sorted) {
         RT_TRY(cnt_leaf.alloc(Q, "select counts"));
         RT_TRY(cnt_rng.alloc(Q, "select counts"));
@@ -693,6 +701,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         SelIO so = unlimited();
         so.offsets = off.p;
         so.out = ids.p;
+        so.order = perm.p;
         if (wq) {
             so.cur_ids = cursors.p;
             RT_TRY(launch_wq(PASS_SCATTER, t, queries, Q, so, flags.p, s));
@@ -709,6 +718,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         so.off_rng = off_rng.p;
         so.leaf_out = leaf.p;
         so.rng_out = rng.p;
+        so.order = perm.p;
         if (wq) {
             so.cur_leaf = cursors.p;
             so.cur_rng = cursors.p + Q;

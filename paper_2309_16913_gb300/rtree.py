@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_E
 LAYOUTS = {"soa": 0, "aos": 1}
 MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
 PRUNES = {"auto": 0, "off": 1, "on": 2}
+ORDERS = {"input": 0, "hilbert": 1}
 
 
 class RTreeError(RuntimeError):
@@ -47,7 +48,8 @@ class rtree_join_opts_t(C.Structure):
 
 
 class rtree_select_opts_t(C.Structure):
-    _fields_ = [("unsorted", C.c_int32), ("mapping", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("unsorted", C.c_int32), ("mapping", C.c_int32), ("order", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class rtree_server_config_t(C.Structure):
@@ -70,13 +72,15 @@ class rtree_server_stats_t(C.Structure):
 
 RTREE_REQ_SELECT, RTREE_REQ_PROBE_JOIN = 0, 1
 RTREE_TUNE_INCLUDE_BUILD = 1
+RTREE_TUNE_ORDERS = 2
 
 
 class rtree_tune_result_t(C.Structure):
     _fields_ = [("fanout", C.c_int32), ("layout", C.c_int32), ("mapping", C.c_int32),
-                ("tried", C.c_int32), ("ms", C.c_double), ("ms_all", C.c_double * 32),
-                ("fanout_all", C.c_int32 * 32), ("layout_all", C.c_int32 * 32),
-                ("mapping_all", C.c_int32 * 32)]
+                ("order", C.c_int32), ("tried", C.c_int32), ("reserved", C.c_int32),
+                ("ms", C.c_double), ("ms_all", C.c_double * 64),
+                ("fanout_all", C.c_int32 * 64), ("layout_all", C.c_int32 * 64),
+                ("mapping_all", C.c_int32 * 64), ("order_all", C.c_int32 * 64)]
 
 
 class rtree_info_t(C.Structure):
@@ -260,13 +264,14 @@ def rtree_export(handle: int, stream=None) -> dict:
 
 
 def rtree_range_select(handle: int, queries, unsorted: bool = False, mapping: str | int = "auto",
-                       stream=None) -> int:
+                       stream=None, order: str | int = "input") -> int:
     """Runs a batched range select; returns the result handle."""
     lib = load_library()
     qp, q, keep = _as_rows(queries, "queries")
     opts = rtree_select_opts_t()
     opts.unsorted = 1 if unsorted else 0
     opts.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
+    opts.order = ORDERS[order] if isinstance(order, str) else int(order)
     out = C.c_void_p()
     _check(lib.rtree_range_select(handle, qp, q, C.byref(opts), _stream(stream), C.byref(out)), lib)
     del keep
@@ -447,9 +452,10 @@ def rtree_server_stop(server: int) -> None:
 
 
 def rtree_autotune(rects, queries, ids=None, fanouts=(16, 32, 64), include_build: bool = True,
-                   stream=None) -> dict:
-    """Times every fanout x layout x mapping on the given sample and returns
-    the fastest configuration plus all times (see the C header)."""
+                   stream=None, orders: bool = False) -> dict:
+    """Times every fanout x layout x mapping (x traversal order with
+    ``orders``) on the given sample and returns the fastest configuration
+    plus all times (see the C header)."""
     lib = load_library()
     rp, n, keep_r = _as_rows(rects, "rects")
     ip, keep_i = _as_ids(ids, n)
@@ -457,14 +463,19 @@ def rtree_autotune(rects, queries, ids=None, fanouts=(16, 32, 64), include_build
     fo = (C.c_int32 * len(fanouts))(*fanouts)
     out = rtree_tune_result_t()
     _check(lib.rtree_autotune(rp, ip, n, qp, q, fo, len(fanouts),
-                              RTREE_TUNE_INCLUDE_BUILD if include_build else 0, _stream(stream),
+                              (RTREE_TUNE_INCLUDE_BUILD if include_build else 0) |
+                              (RTREE_TUNE_ORDERS if orders else 0), _stream(stream),
                               C.byref(out)), lib)
     del keep_r, keep_i, keep_q
     names = {v: k for k, v in MAPPINGS.items()}
     lays = {v: k for k, v in LAYOUTS.items()}
+    ords = {v: k for k, v in ORDERS.items()}
+
+    def key(f, l, m, o):
+        return f"F{f}_{lays[l]}_{names[m]}" + ("_hilbert" if o else "")
     return {"fanout": out.fanout, "layout": lays[out.layout], "mapping": names[out.mapping],
-            "ms": out.ms,
-            "all": {f"F{out.fanout_all[i]}_{lays[out.layout_all[i]]}_{names[out.mapping_all[i]]}":
+            "order": ords[out.order], "ms": out.ms,
+            "all": {key(out.fanout_all[i], out.layout_all[i], out.mapping_all[i], out.order_all[i]):
                     round(out.ms_all[i], 3) for i in range(out.tried)}}
 
 
@@ -644,8 +655,9 @@ class RTree:
     def export(self, stream=None) -> dict:
         return rtree_export(self.handle, stream)
 
-    def range_select(self, queries, unsorted: bool = False, mapping="auto", stream=None) -> Result:
-        return Result(rtree_range_select(self.handle, queries, unsorted, mapping, stream))
+    def range_select(self, queries, unsorted: bool = False, mapping="auto", stream=None,
+                     order="input") -> Result:
+        return Result(rtree_range_select(self.handle, queries, unsorted, mapping, stream, order))
 
     def select_stats(self, queries, stream=None) -> dict:
         return rtree_range_select_stats(self.handle, queries, stream)

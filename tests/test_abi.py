@@ -58,7 +58,10 @@ def test_struct_layouts_match_header(tmp_path):
                    " offsetof(rtree_server_config_t, max_batch_ids), sizeof(rtree_reply_t),"
                    " offsetof(rtree_reply_t, latency_us), sizeof(rtree_server_stats_t)); "
                    "printf(\"%zu %zu %zu %zu\\n\", offsetof(rtree_config_t, sort_children), sizeof(rtree_join_opts_t),"
-                   " offsetof(rtree_info_t, sort_children), (size_t)RTREE_PRUNE_ON); return 0;}\n")
+                   " offsetof(rtree_info_t, sort_children), (size_t)RTREE_PRUNE_ON); "
+                   "printf(\"%zu %zu\\n\", offsetof(rtree_select_opts_t, order), (size_t)RTREE_ORDER_HILBERT); "
+                   "printf(\"%zu %zu %zu\\n\", sizeof(rtree_tune_result_t), offsetof(rtree_tune_result_t, ms_all),"
+                   " offsetof(rtree_tune_result_t, order_all)); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
@@ -67,7 +70,10 @@ def test_struct_layouts_match_header(tmp_path):
             C.sizeof(rt.rtree_server_config_t), rt.rtree_server_config_t.max_batch_ids.offset,
             C.sizeof(rt.rtree_reply_t), rt.rtree_reply_t.latency_us.offset,
             C.sizeof(rt.rtree_server_stats_t), rt.rtree_config_t.sort_children.offset,
-            C.sizeof(rt.rtree_join_opts_t), rt.rtree_info_t.sort_children.offset, rt.PRUNES["on"]]
+            C.sizeof(rt.rtree_join_opts_t), rt.rtree_info_t.sort_children.offset, rt.PRUNES["on"],
+            rt.rtree_select_opts_t.order.offset, rt.ORDERS["hilbert"],
+            C.sizeof(rt.rtree_tune_result_t), rt.rtree_tune_result_t.ms_all.offset,
+            rt.rtree_tune_result_t.order_all.offset]
     assert got == want
 
 
