@@ -308,6 +308,8 @@ def run_ours(args):
         seg = np.diff(res.offsets_tensor().cpu().numpy())
         res.close()
         order_cmp = None if args.no_order else compare_orders(rt, torch, t, queries, stream, mapping)
+    layout_cmp = None if args.no_order else compare_layouts(rt, torch, rects, ids, queries, stream, F,
+                                                            mapping, order)
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
     breakdown = {}
@@ -449,6 +451,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "join": join,
             "query_order": order_cmp,
+            "layouts": layout_cmp,
             "uneven": uneven,
             "serve": serve,
             "select_stats": stats,
@@ -482,6 +485,28 @@ def compare_orders(rt, torch, tree, queries, stream, mapping, reps=3):
         out[order] = {"ms_per_select": round(e0.elapsed_time(e1) / reps, 3),
                       "traversal_ms": round(trav, 3)}
     out["what"] = "1M-query select on the built tree, no build; traversal = select_count + select_desc"
+    return out
+
+
+def compare_layouts(rt, torch, rects, ids, queries, stream, F, mapping, order, reps=3):
+    """Traversal kernel time (count + descriptor passes) of the same select
+    on trees built in each node layout: D0 (aos), D1 (soa), D2 (lohi)."""
+    out = {}
+    for layout in ("aos", "soa", "lohi"):
+        with rt.RTree(rects, ids, fanout=F, layout=layout, stream=stream) as t:
+            for _ in range(2):
+                t.range_select(queries, mapping=mapping, stream=stream, order=order).close()
+            torch.cuda.synchronize()
+            rt.rtree_timing_reset()
+            rt.rtree_timing_enable(True)
+            for _ in range(reps):
+                t.range_select(queries, mapping=mapping, stream=stream, order=order).close()
+            torch.cuda.synchronize()
+            rt.rtree_timing_enable(False)
+            k = rt.rtree_timing_get()
+        out[layout] = {n: round(v[1] / reps, 3) for n, v in k.items()
+                       if n in ("select_count", "select_desc")}
+    out["what"] = f"F={F}, {mapping}, {order} order: traversal kernel ms per 1M-query select"
     return out
 
 

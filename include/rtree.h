@@ -60,8 +60,10 @@ typedef enum rtree_status {
 
 /* Node layouts (Section 2.3).  SOA is layout D1: per node, the F lower-x
  * values, then F lower-y, F upper-x, F upper-y.  AOS is layout D0: per node,
- * F entries of 16 bytes each (xmin, ymin, xmax, ymax). */
-enum { RTREE_LAYOUT_SOA = 0, RTREE_LAYOUT_AOS = 1 };
+ * F entries of 16 bytes each (xmin, ymin, xmax, ymax).  LOHI is layout D2:
+ * per node, the F lower-left points (xmin, ymin), then the F upper-right
+ * points (xmax, ymax). */
+enum { RTREE_LAYOUT_SOA = 0, RTREE_LAYOUT_AOS = 1, RTREE_LAYOUT_LOHI = 2 };
 
 /* How range-select work is spread over the GPU. */
 enum {
@@ -397,7 +399,7 @@ RTREE_API const char *rtree_version(void);
  * rtree_autotune -- choose fanout, node layout and thread mapping by timing.
  *
  * Builds a tree over rects/ids for every fanout in fanouts[0 .. n_fanouts)
- * (NULL or 0 -> {16, 32, 64}; at most 8) and both layouts, and times a
+ * (NULL or 0 -> {16, 32, 64}; at most 8) and all three layouts, and times a
  * sorted rtree_range_select of the q queries under both mappings with CUDA
  * events on `stream` (one untimed run first).  flags & RTREE_TUNE_INCLUDE_BUILD
  * adds the build time to each configuration's time; flags & RTREE_TUNE_ORDERS

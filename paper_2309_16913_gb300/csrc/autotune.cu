@@ -39,7 +39,7 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
     double best = 1e300;
     int k = 0;
     for (int fi = 0; fi < n_fanouts && st == RTREE_OK; ++fi) {
-        for (int layout = RTREE_LAYOUT_SOA; layout <= RTREE_LAYOUT_AOS && st == RTREE_OK; ++layout) {
+        for (int layout = RTREE_LAYOUT_SOA; layout <= RTREE_LAYOUT_LOHI && st == RTREE_OK; ++layout) {
             rtree_config_t cfg{};
             cfg.fanout = fanouts[fi];
             cfg.layout = layout;

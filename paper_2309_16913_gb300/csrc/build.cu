@@ -207,6 +207,10 @@ __global__ void k_layout(int F, int layout, int64_t P, int64_t m,
         }
         if (layout == RTREE_LAYOUT_AOS) {
             reinterpret_cast<float4 *>(mbr)[g * F + j] = b;
+        } else if (layout == RTREE_LAYOUT_LOHI) {
+            float2 *p = reinterpret_cast<float2 *>(mbr + g * 4 * F);
+            p[j] = make_float2(b.x, b.y);
+            p[F + j] = make_float2(b.z, b.w);
         } else {
             float *p = mbr + g * 4 * F + j;
             p[0] = b.x;

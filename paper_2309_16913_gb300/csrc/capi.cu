@@ -193,7 +193,7 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
         return fail(RTREE_EINVAL, "rtree_build: sort_children must be 0 or 1");
     if (!fanout_ok(F))
         return fail(RTREE_EINVAL, "rtree_build: fanout %d not in {4,8,16,32,64,128}", F);
-    if (layout != RTREE_LAYOUT_SOA && layout != RTREE_LAYOUT_AOS)
+    if (layout != RTREE_LAYOUT_SOA && layout != RTREE_LAYOUT_AOS && layout != RTREE_LAYOUT_LOHI)
         return fail(RTREE_EINVAL, "rtree_build: unknown layout %d", layout);
     try {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -304,6 +304,12 @@ rtree_status rtree_export(const rtree_t *t, int64_t *level_nodes, int32_t *count
                 float *o = mbrs + (g * F + j) * 4;
                 if (t->layout == RTREE_LAYOUT_AOS) {
                     memcpy(o, raw + (g * F + j) * 4, 16);
+                } else if (t->layout == RTREE_LAYOUT_LOHI) {
+                    const float *b = raw + g * 4 * F;
+                    o[0] = b[2 * j];
+                    o[1] = b[2 * j + 1];
+                    o[2] = b[2 * F + 2 * j];
+                    o[3] = b[2 * F + 2 * j + 1];
                 } else {
                     const float *b = raw + g * 4 * F + j;
                     o[0] = b[0];

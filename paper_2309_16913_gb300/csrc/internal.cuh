@@ -195,6 +195,11 @@ __device__ __forceinline__ float4 load_entry(const float *__restrict__ mbr, int 
 {
     if (layout == RTREE_LAYOUT_AOS)
         return __ldg(reinterpret_cast<const float4 *>(mbr) + g * F + j);
+    if (layout == RTREE_LAYOUT_LOHI) {
+        const float2 *p = reinterpret_cast<const float2 *>(mbr + g * 4 * F);
+        const float2 lo = __ldg(p + j), hi = __ldg(p + F + j);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
     const float *b = mbr + g * 4 * F + j;
     return make_float4(__ldg(b), __ldg(b + F), __ldg(b + 2 * F), __ldg(b + 3 * F));
 }
@@ -204,6 +209,11 @@ __device__ __forceinline__ float4 load_entry_t(const float *__restrict__ mbr, in
 {
     if (LAYOUT == RTREE_LAYOUT_AOS)
         return __ldg(reinterpret_cast<const float4 *>(mbr) + g * F + j);
+    if (LAYOUT == RTREE_LAYOUT_LOHI) {
+        const float2 *p = reinterpret_cast<const float2 *>(mbr + g * 4 * F);
+        const float2 lo = __ldg(p + j), hi = __ldg(p + F + j);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
     const float *b = mbr + g * 4 * F + j;
     return make_float4(__ldg(b), __ldg(b + F), __ldg(b + 2 * F), __ldg(b + 3 * F));
 }

@@ -109,6 +109,8 @@ __device__ __forceinline__ float entry_lx(const TreeDev &t, int64_t g, int j)
 {
     if (t.layout == RTREE_LAYOUT_AOS)
         return __ldg(reinterpret_cast<const float *>(t.mbr) + (g * t.fanout + j) * 4);
+    if (t.layout == RTREE_LAYOUT_LOHI)
+        return __ldg(t.mbr + g * 4 * t.fanout + 2 * j);
     return __ldg(t.mbr + g * 4 * t.fanout + j);
 }
 

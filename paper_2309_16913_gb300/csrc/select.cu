@@ -475,8 +475,9 @@ SelectKernel pick_pass(int pass)
 template <int F>
 SelectKernel pick_layout(int layout, int pass)
 {
-    return layout == RTREE_LAYOUT_AOS ? pick_pass<F, RTREE_LAYOUT_AOS>(pass)
-                                      : pick_pass<F, RTREE_LAYOUT_SOA>(pass);
+    return layout == RTREE_LAYOUT_AOS    ? pick_pass<F, RTREE_LAYOUT_AOS>(pass)
+           : layout == RTREE_LAYOUT_LOHI ? pick_pass<F, RTREE_LAYOUT_LOHI>(pass)
+                                         : pick_pass<F, RTREE_LAYOUT_SOA>(pass);
 }
 
 SelectKernel pick(int F, int layout, int pass)
@@ -536,8 +537,9 @@ WqKernel pick_wq_pass(int pass)
 template <int F>
 WqKernel pick_wq_layout(int layout, int pass)
 {
-    return layout == RTREE_LAYOUT_AOS ? pick_wq_pass<F, RTREE_LAYOUT_AOS>(pass)
-                                      : pick_wq_pass<F, RTREE_LAYOUT_SOA>(pass);
+    return layout == RTREE_LAYOUT_AOS    ? pick_wq_pass<F, RTREE_LAYOUT_AOS>(pass)
+           : layout == RTREE_LAYOUT_LOHI ? pick_wq_pass<F, RTREE_LAYOUT_LOHI>(pass)
+                                         : pick_wq_pass<F, RTREE_LAYOUT_SOA>(pass);
 }
 
 WqKernel pick_wq(int F, int layout, int pass)

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librtree.so")
 RTREE_OK, RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA, RTREE_ETIMEOUT, RTREE_EOVERFLOW, RTREE_EINTERNAL = range(7)
 STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_ECUDA",
                 4: "RTREE_ETIMEOUT", 5: "RTREE_EOVERFLOW", 6: "RTREE_EINTERNAL"}
-LAYOUTS = {"soa": 0, "aos": 1}
+LAYOUTS = {"soa": 0, "aos": 1, "lohi": 2}
 MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
 PRUNES = {"auto": 0, "off": 1, "on": 2}
 ORDERS = {"input": 0, "hilbert": 1}

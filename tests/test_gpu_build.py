@@ -26,7 +26,7 @@ def export_gpu(rt, rects, ids, F, layout):
         return t.export(), t.info()
 
 
-@pytest.mark.parametrize("layout", ["soa", "aos"])
+@pytest.mark.parametrize("layout", ["soa", "aos", "lohi"])
 @pytest.mark.parametrize("F", [4, 8, 16, 32, 64, 128])
 def test_tree_matches_oracle(rt, F, layout):
     for kind, n in (("uniform", 1), ("grid", F + 1), ("clustered", 4099), ("dups", 20011),
@@ -104,7 +104,7 @@ def test_injected_allocation_failures_recover(rt):
 def test_autotune_returns_a_measured_choice(rt):
     w = dg.workload("scaled", n=300_000, q=4000)
     tune = rt.rtree_autotune(w.rects, w.queries, w.ids, fanouts=(16, 64))
-    assert len(tune["all"]) == 2 * 2 * 2
+    assert len(tune["all"]) == 2 * 3 * 2
     key = f"F{tune['fanout']}_{tune['layout']}_{tune['mapping']}"
     assert tune["all"][key] == min(tune["all"].values()) and tune["ms"] > 0
     # the chosen configuration still answers exactly

@@ -55,7 +55,7 @@ def test_scaled_10m_1m_queries(rt, F):
     t_orc = oracle.Tree(w.rects, w.ids, F)
     rng = np.random.default_rng(100 + F)
     sample = np.sort(rng.choice(w.queries.shape[0], 1500, replace=False))
-    for layout in ("soa", "aos"):
+    for layout in ("soa", "aos", "lohi"):
         with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(),
                       fanout=F, layout=layout) as t:
             total = check_sample(rt, t, t_orc, w.queries, sample, F)

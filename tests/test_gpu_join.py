@@ -43,7 +43,7 @@ def test_join_random(rt, kind):
     want = oracle.brute_join(r, s, rid, sid) if kind != "dups" else \
         oracle.Tree(r, rid, 16).join(oracle.Tree(s, sid, 16))
     for fr, fs, lr, ls in ((16, 16, "soa", "soa"), (32, 4, "aos", "soa"), (4, 64, "soa", "aos"),
-                           (128, 8, "aos", "aos")):
+                           (128, 8, "aos", "aos"), (32, 16, "lohi", "soa"), (8, 32, "aos", "lohi")):
         got = join_gpu(rt, r, rid, s, sid, fr, fs, lr, ls)
         assert np.array_equal(got, want), (kind, fr, fs, lr, ls)
 

@@ -31,7 +31,7 @@ def pruned_gpu(rt, r, rid, s, sid, fr, fs, lr="soa", ls="soa", prune="on"):
             res.close()
 
 
-@pytest.mark.parametrize("layout", ["soa", "aos"])
+@pytest.mark.parametrize("layout", ["soa", "aos", "lohi"])
 @pytest.mark.parametrize("F", [4, 8, 16, 32, 64, 128])
 def test_sorted_tree_matches_oracle(rt, F, layout):
     for kind, n in (("grid", 5000), ("dups", 20011), ("clustered", 4099), ("negative", 70001), ("uniform", 1)):
@@ -92,7 +92,8 @@ def test_pruned_join_random(rt, kind):
         oracle.Tree(s, sid, 16, sort_children=True))
     assert np.array_equal(got_o, want)
     for fr, fs, lr, ls in ((16, 16, "soa", "soa"), (32, 4, "aos", "soa"), (4, 64, "soa", "aos"),
-                           (128, 8, "aos", "aos"), (8, 128, "soa", "soa"), (64, 64, "aos", "soa")):
+                           (128, 8, "aos", "aos"), (8, 128, "soa", "soa"), (64, 64, "aos", "soa"),
+                           (32, 32, "lohi", "lohi"), (16, 64, "lohi", "aos")):
         got = pruned_gpu(rt, r, rid, s, sid, fr, fs, lr, ls)
         assert np.array_equal(got, want), (kind, fr, fs, lr, ls)
 

@@ -17,7 +17,7 @@ def rt():
 
 
 @pytest.mark.parametrize("mapping", ["warp_per_query", "work_queue"])
-@pytest.mark.parametrize("F,layout", [(16, "soa"), (64, "aos"), (4, "aos"), (128, "soa")])
+@pytest.mark.parametrize("F,layout", [(16, "soa"), (64, "aos"), (4, "aos"), (128, "soa"), (32, "lohi")])
 def test_hilbert_order_matches_oracle(rt, F, layout, mapping):
     w = dg.workload("scaled", n=300_000, q=20_000)
     want = oracle.Tree(w.rects, w.ids, F).select(w.queries)
@@ -73,8 +73,8 @@ def test_plan_refuses_order(rt):
 def test_autotune_tries_orders(rt):
     w = dg.workload("scaled", n=200_000, q=3000)
     tune = rt.rtree_autotune(w.rects, w.queries, w.ids, fanouts=(16, 64), orders=True)
-    assert len(tune["all"]) == 2 * 2 * 2 * 2
-    assert sum(k.endswith("_hilbert") for k in tune["all"]) == 8
+    assert len(tune["all"]) == 2 * 3 * 2 * 2
+    assert sum(k.endswith("_hilbert") for k in tune["all"]) == 12
     assert tune["order"] in ("input", "hilbert") and abs(tune["ms"] - min(tune["all"].values())) < 1e-3
     want = oracle.Tree(w.rects, w.ids, tune["fanout"]).select(w.queries)
     got = select_gpu(rt, w.rects, w.ids, w.queries, tune["fanout"], tune["layout"],

@@ -31,7 +31,7 @@ def test_predicate_golden_cases(rt):
         assert len(got) == exp, (b, a, exp)
 
 
-@pytest.mark.parametrize("layout", ["soa", "aos"])
+@pytest.mark.parametrize("layout", ["soa", "aos", "lohi"])
 @pytest.mark.parametrize("F", [4, 8, 16])
 def test_select_golden(rt, F, layout):
     rects, ids, queries, expected = golden_io.select_case()
@@ -40,7 +40,7 @@ def test_select_golden(rt, F, layout):
         assert np.array_equal(got[off[i]:off[i + 1]], e), (i, F, layout)
 
 
-@pytest.mark.parametrize("layout", ["soa", "aos"])
+@pytest.mark.parametrize("layout", ["soa", "aos", "lohi"])
 @pytest.mark.parametrize("F", FANOUTS)
 def test_plain_workload_full_size(rt, F, layout):
     """100k uniform rectangles, 1k queries: every query checked."""
@@ -59,7 +59,7 @@ def test_random_kinds(rt, kind, F):
     ids = np.random.default_rng(1).permutation(n).astype(np.int32) - np.int32(12345)
     queries = random_case(kind, 700, 4)
     want = oracle.Tree(rects, ids, F).select(queries)
-    for layout in ("soa", "aos"):
+    for layout in ("soa", "aos", "lohi"):
         got = select_gpu(rt, rects, ids, queries, fanout=F, layout=layout)
         assert_csr_equal(got, want, f"{kind} F={F} {layout}")
 
@@ -210,7 +210,7 @@ def test_work_queue_mapping(rt, unsorted):
     them) gives the same result sets as the oracle; heavy queries included."""
     w = dg.workload("uneven", n=400_000, q=6000)
     want = oracle.Tree(w.rects, w.ids, 16).select(w.queries)
-    for F, layout in ((16, "soa"), (64, "aos"), (4, "soa")):
+    for F, layout in ((16, "soa"), (64, "aos"), (4, "soa"), (32, "lohi")):
         off, ids = select_gpu(rt, w.rects, w.ids, w.queries, fanout=F, layout=layout,
                               mapping="work_queue", unsorted=unsorted)
         assert np.array_equal(off, want[0]), (F, layout)
