@@ -58,6 +58,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-join", action="store_true")
     ap.add_argument("--no-order", action="store_true")
+    ap.add_argument("--no-persist", action="store_true")
     ap.add_argument("--order", choices=["auto", "input", "hilbert"], default="auto",
                     help="traversal order of the query batch (auto: the autotuner picks)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -310,6 +311,7 @@ def run_ours(args):
         order_cmp = None if args.no_order else compare_orders(rt, torch, t, queries, stream, mapping)
     layout_cmp = None if args.no_order else compare_layouts(rt, torch, rects, ids, queries, stream, F,
                                                             mapping, order)
+    persist = None if args.no_persist else run_persist(rt, torch, rects, ids, queries, F, layout, rank)
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
     breakdown = {}
@@ -452,6 +454,7 @@ def run_ours(args):
             "join": join,
             "query_order": order_cmp,
             "layouts": layout_cmp,
+            "persist": persist,
             "uneven": uneven,
             "serve": serve,
             "select_stats": stats,
@@ -486,6 +489,36 @@ def compare_orders(rt, torch, tree, queries, stream, mapping, reps=3):
                       "traversal_ms": round(trav, 3)}
     out["what"] = "1M-query select on the built tree, no build; traversal = select_count + select_desc"
     return out
+
+
+def run_persist(rt, torch, rects, ids, queries, F, layout, rank):
+    """Save the built 10M tree to a file and load it back (the serving
+    restart path); the file sits in the page cache, so this times the
+    library's write/read, checksum and copy path, not the disk."""
+    import tempfile
+    path = os.path.join(tempfile.gettempdir(), f"bench_rank{rank}_{os.getpid()}.rtree")
+    t = rt.RTree(rects, ids, fanout=F, layout=layout)
+    try:
+        t0 = time.perf_counter()
+        t.save(path)
+        save_s = time.perf_counter() - t0
+        size = os.path.getsize(path)
+        t0 = time.perf_counter()
+        t2 = rt.RTree.load(path)
+        torch.cuda.synchronize()
+        load_s = time.perf_counter() - t0
+        a = t.range_select(queries[:20000])
+        b = t2.range_select(queries[:20000])
+        same = bool(torch.equal(a.offsets_tensor(), b.offsets_tensor()) and
+                    torch.equal(a.ids_tensor(), b.ids_tensor()))
+        a.close(); b.close(); t2.close()
+    finally:
+        t.close()
+        if os.path.exists(path):
+            os.remove(path)
+    return {"file_bytes": size, "save_ms": round(save_s * 1e3, 1), "load_ms": round(load_s * 1e3, 1),
+            "load_gbs": round(size / load_s / 1e9, 2), "loaded_tree_answers_same": same,
+            "what": "rtree_save / rtree_load of the bench's tree via the page cache (host wall clock)"}
 
 
 def compare_layouts(rt, torch, rects, ids, queries, stream, F, mapping, order, reps=3):

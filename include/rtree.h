@@ -55,7 +55,8 @@ typedef enum rtree_status {
     RTREE_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error) */
     RTREE_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
     RTREE_EOVERFLOW = 5, /* a size exceeds a fixed capacity (message says which) */
-    RTREE_EINTERNAL = 6  /* a device-side consistency check failed */
+    RTREE_EINTERNAL = 6, /* a device-side consistency check failed */
+    RTREE_EIO = 7        /* a file could not be opened, read or written (rtree_save/load) */
 } rtree_status;
 
 /* Node layouts (Section 2.3).  SOA is layout D1: per node, the F lower-x
@@ -418,6 +419,29 @@ typedef struct rtree_tune_result {
     int32_t mapping_all[64];
     int32_t order_all[64];
 } rtree_tune_result_t;
+
+/*
+ * rtree_save / rtree_load -- keep a built tree in a file (an addition: the
+ * paper's index lives in memory only; a serving process restarts from the
+ * file instead of rebuilding).
+ *
+ * The file is a 1 KiB little-endian header (magic "RTREEGB3", version 1,
+ * fanout, layout, sorted flag, level sizes, root MBR, payload size and
+ * checksums) followed by the node entries, node metadata, node boxes and
+ * leaf-entry ids exactly as held on the device.  rtree_save waits for the
+ * tree's stream work, writes a temporary file beside `path` and renames it,
+ * so `path` is only ever replaced by a complete file.  rtree_load reads and
+ * checks the header and the file size before any device work, copies the
+ * payload to `device` (-1: the current device) through pinned staging
+ * buffers, verifies the payload checksum and checks on the device that the
+ * node structure is a tree (children in the next level, entry ranges inside
+ * the leaf level).  The loaded tree answers every call as the saved one.
+ * Errors: RTREE_EIO (cannot open, read, write or rename), RTREE_EINVAL (not
+ * a tree file of this version, wrong size, checksum or structure mismatch:
+ * nothing is returned), RTREE_ENOMEM, RTREE_ECUDA.
+ */
+RTREE_API rtree_status rtree_save(const rtree_t *tree, const char *path, void *stream);
+RTREE_API rtree_status rtree_load(const char *path, int device, void *stream, rtree_t **out);
 
 RTREE_API rtree_status rtree_autotune(const float *rects, const int32_t *ids, int64_t n,
                                       const float *queries, int64_t q, const int32_t *fanouts,

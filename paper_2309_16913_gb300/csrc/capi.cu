@@ -31,7 +31,7 @@ rtree_status fail(rtree_status st, const char *fmt, ...)
 
 void clear_error() { g_err.clear(); }
 
-static void setup_device_pool(int dev)
+void setup_device_pool(int dev)
 {
     static std::mutex mu;
     static bool done[64] = {};
@@ -88,23 +88,6 @@ int sm_count()
 
 namespace {
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (dev != prev)
-            cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev)
-            cudaSetDevice(prev);
-    }
-};
-
 // Where a pointer lives: 1 = device memory usable by kernels, 0 = host.
 int pointer_kind(const void *p, int *device)
 {
@@ -143,6 +126,8 @@ rtree_status stage(const void *p, size_t bytes, size_t align, cudaStream_t s, De
     return RTREE_OK;
 }
 
+}  // namespace
+
 void free_tree_arrays(rtree *t)
 {
     if (t->mbr)
@@ -161,7 +146,6 @@ void free_tree_arrays(rtree *t)
 
 bool fanout_ok(int f) { return f == 4 || f == 8 || f == 16 || f == 32 || f == 64 || f == 128; }
 
-}  // namespace
 }  // namespace rt
 
 using namespace rt;

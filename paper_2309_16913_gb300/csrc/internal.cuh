@@ -38,6 +38,29 @@ void clear_error();
 // host-side counter can make the k-th allocation fail (fault injection for
 // tests; no GPU fault is involved).
 rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what);
+// Keeps freed blocks in the device's default pool between calls (once per device).
+void setup_device_pool(int dev);
+// Releases a tree's device arrays (not the struct).
+void free_tree_arrays(rtree *t);
+bool fanout_ok(int f);
+
+// Makes `dev` current for the scope, restoring the previous device after.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (dev != prev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
 void dfree(void *p, cudaStream_t s);
 
 template <typename T>

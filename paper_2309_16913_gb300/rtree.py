@@ -23,9 +23,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librtree.so")
 
-RTREE_OK, RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA, RTREE_ETIMEOUT, RTREE_EOVERFLOW, RTREE_EINTERNAL = range(7)
+(RTREE_OK, RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA, RTREE_ETIMEOUT, RTREE_EOVERFLOW, RTREE_EINTERNAL,
+ RTREE_EIO) = range(8)
 STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_ECUDA",
-                4: "RTREE_ETIMEOUT", 5: "RTREE_EOVERFLOW", 6: "RTREE_EINTERNAL"}
+                4: "RTREE_ETIMEOUT", 5: "RTREE_EOVERFLOW", 6: "RTREE_EINTERNAL", 7: "RTREE_EIO"}
 LAYOUTS = {"soa": 0, "aos": 1, "lohi": 2}
 MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
 PRUNES = {"auto": 0, "off": 1, "on": 2}
@@ -104,6 +105,8 @@ def _bind(lib):
         "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
         "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
         "rtree_join_ex": (C.c_int, [vp, vp, vp, vp, C.POINTER(vp)]),
+        "rtree_save": (C.c_int, [vp, C.c_char_p, vp]),
+        "rtree_load": (C.c_int, [C.c_char_p, C.c_int, vp, C.POINTER(vp)]),
         "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
         "rtree_range_select_noalloc": (C.c_int, [vp, vp, i64, vp, vp, i64, C.POINTER(C.c_int64), vp]),
         "rtree_result_total": (i64, [vp]),
@@ -231,6 +234,20 @@ def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", st
     out = C.c_void_p()
     _check(lib.rtree_build(rp, ip, n, C.byref(cfg), _stream(stream), C.byref(out)), lib)
     del keep_r, keep_i
+    return out.value
+
+
+def rtree_save(handle: int, path: str, stream=None) -> None:
+    """Writes the tree to ``path`` (atomically; see the C header)."""
+    lib = load_library()
+    _check(lib.rtree_save(handle, os.fsencode(path), _stream(stream)), lib)
+
+
+def rtree_load(path: str, device: int = -1, stream=None) -> int:
+    """Loads a tree saved by rtree_save; returns the handle."""
+    lib = load_library()
+    out = C.c_void_p()
+    _check(lib.rtree_load(os.fsencode(path), int(device), _stream(stream), C.byref(out)), lib)
     return out.value
 
 
@@ -651,6 +668,16 @@ class RTree:
 
     def info(self) -> dict:
         return rtree_get_info(self.handle)
+
+    def save(self, path: str, stream=None) -> None:
+        rtree_save(self.handle, path, stream)
+
+    @classmethod
+    def load(cls, path: str, device: int = -1, stream=None) -> "RTree":
+        t = cls.__new__(cls)
+        t.handle = None
+        t.handle = rtree_load(path, device, stream)
+        return t
 
     def export(self, stream=None) -> dict:
         return rtree_export(self.handle, stream)
