@@ -340,20 +340,19 @@ def run_ours(args):
     # ---- end to end through the C ABI with host (pinned) buffers
     e2e = None
     if not args.no_e2e:
-        lib = rt.load_library()
         h_rects = torch.from_numpy(w.rects).pin_memory()
         h_ids = torch.from_numpy(w.ids).pin_memory()
         h_q = torch.from_numpy(w.queries).pin_memory()
         h_off = torch.empty(Q + 1, dtype=torch.int64).pin_memory()
         h_out = torch.empty(max(1, int(total_hits)), dtype=torch.int32).pin_memory()
-        sptr = stream.cuda_stream
 
         def e2e_step():
+            # host rects/ids/queries in, host offsets/ids out; the result
+            # copy overlaps the select of later chunks (rtree_range_select_host)
             h = rt.rtree_build(h_rects, h_ids, F, layout, stream)
-            r = rt.rtree_range_select(h, h_q, mapping=mapping, stream=stream, order=order)
-            rc = lib.rtree_result_copy_to_host(r, h_off.data_ptr(), h_out.data_ptr(), sptr)
-            assert rc == 0, rt.rtree_last_error()
-            rt.rtree_result_free(r)
+            tot = rt.rtree_range_select_host(h, h_q, h_off, h_out, mapping=mapping, order=order,
+                                             stream=stream)
+            assert tot == total_hits
             rt.rtree_free(h)
 
         e2e_step()

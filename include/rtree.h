@@ -344,6 +344,25 @@ RTREE_API rtree_status rtree_range_select_stats(const rtree_t *tree, const float
  * 4.1).  The trees may have different fanouts and layouts but must be on the
  * same device.  Errors: RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA.
  */
+/*
+ * rtree_range_select_host -- rtree_range_select with the result written to
+ * caller-owned host memory, the copy overlapped with the work.  One count
+ * pass over the batch fixes every query's offset (written to `offsets`
+ * first); the batch is then cut into chunks of about equal id counts, and
+ * while the second pass and sort of one chunk run on `stream`, the ids of
+ * the chunk before are copied to `ids` on a second stream.  Same ids, order
+ * and options as rtree_range_select.
+ * queries: q*4 floats, host or device.  offsets: host int64[q+1].  ids: host
+ * int32[capacity]; page-locked memory lets the copies overlap the work.
+ * *total receives the number of ids.  If it exceeds capacity the call
+ * returns RTREE_EOVERFLOW with offsets and *total written and ids untouched
+ * (resize and call again).  Errors otherwise as rtree_range_select.
+ */
+RTREE_API rtree_status rtree_range_select_host(const rtree_t *tree, const float *queries, int64_t q,
+                                               const rtree_select_opts_t *opts, void *stream,
+                                               int64_t *offsets, int32_t *ids, int64_t capacity,
+                                               int64_t *total);
+
 RTREE_API rtree_status rtree_join(const rtree_t *r, const rtree_t *s, void *stream, rtree_result_t **out);
 
 /*

@@ -366,6 +366,44 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
     }
 }
 
+rtree_status rtree_range_select_host(const rtree_t *t, const float *queries, int64_t q,
+                                     const rtree_select_opts_t *opts, void *stream, int64_t *offsets,
+                                     int32_t *ids, int64_t capacity, int64_t *total)
+{
+    clear_error();
+    if (!t || !offsets || !total || capacity < 0 || (capacity > 0 && !ids))
+        return fail(RTREE_EINVAL, "rtree_range_select_host: bad argument");
+    *total = 0;
+    if (q < 0 || q >= (int64_t)INT32_MAX)
+        return fail(RTREE_EINVAL, "rtree_range_select_host: q = %lld out of range", (long long)q);
+    if (q > 0 && !queries)
+        return fail(RTREE_EINVAL, "rtree_range_select_host: queries is NULL");
+    const bool sorted = !(opts && opts->unsorted);
+    const int mapping = opts ? opts->mapping : RTREE_MAP_AUTO;
+    if (mapping < RTREE_MAP_AUTO || mapping > RTREE_MAP_WORK_QUEUE)
+        return fail(RTREE_EINVAL, "rtree_range_select_host: unknown mapping %d", mapping);
+    const int order = opts ? opts->order : RTREE_ORDER_INPUT;
+    if (order != RTREE_ORDER_INPUT && order != RTREE_ORDER_HILBERT)
+        return fail(RTREE_EINVAL, "rtree_range_select_host: unknown order %d", order);
+    try {
+        DeviceGuard guard(t->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        DevBuf<float4> qtmp(s);
+        const float4 *dq = nullptr;
+        RT_TRY(stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq));
+        rtree_status st = range_select_host(t, dq, q, sorted, mapping, order, s, offsets, ids, capacity, total);
+        if (st == RTREE_OK) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess)
+                st = fail(RTREE_ECUDA, "rtree_range_select_host: %s", cudaGetErrorString(e));
+        }
+        timing_resolve();
+        return st;
+    } catch (...) {
+        return fail(RTREE_ENOMEM, "rtree_range_select_host: host allocation failed");
+    }
+}
+
 rtree_status rtree_range_select_stats(const rtree_t *t, const float *queries, int64_t q, void *stream,
                                       int64_t stats[8])
 {

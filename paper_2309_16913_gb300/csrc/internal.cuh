@@ -322,9 +322,13 @@ struct SortSources {
 // Writes segment i's ids, sorted ascending (signed), to
 // out[off[i] .. off[i+1]).  out may be the leaf array itself (in place).
 // Enqueues work only (no host synchronization); `total` must bound the sum
-// of all segment lengths.  Device-side capacity problems set bits in *flags.
+// of the segments' lengths (it sizes the scratch), and segments ending past
+// out_cap (default: total) in `out` are skipped.  Offsets may be absolute
+// positions in a larger `out`, so a run of segments can be sorted on its
+// own.  Device-side capacity problems set bits in *flags.
 rtree_status segmented_sort_gather(int32_t *out, const int64_t *off, int64_t nseg, int64_t total,
-                                   const SortSources &src, cudaStream_t s, int32_t *flags);
+                                   const SortSources &src, cudaStream_t s, int32_t *flags,
+                                   int64_t out_cap = -1);
 
 // Sorts every segment ids[offsets[i] .. offsets[i+1]) ascending, in place.
 rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
@@ -334,6 +338,12 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
 // NULL); sort_children orders every node's entries by ascending lx.
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int fanout, int layout,
                         bool sort_children, cudaStream_t s, rtree *t);
+
+// Range select whose result is copied, chunk by chunk, to host memory while
+// later chunks are still being selected (see rtree_range_select_host).
+rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t q, bool sorted,
+                               int mapping, int order, cudaStream_t s, int64_t *h_off, int32_t *h_ids,
+                               int64_t capacity, int64_t *h_total);
 
 // Range select for device queries (float4 rows); order is RTREE_ORDER_*.
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,

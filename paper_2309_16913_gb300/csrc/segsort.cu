@@ -1019,10 +1019,12 @@ rtree_status launch_warp(const int32_t *list, const unsigned long long *count, i
 }  // namespace
 
 rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t nseg, int64_t total,
-                                   const SortSources &S, cudaStream_t s, int32_t *flags)
+                                   const SortSources &S, cudaStream_t s, int32_t *flags, int64_t out_cap)
 {
     if (nseg <= 0 || total <= 0)
         return RTREE_OK;
+    if (out_cap < 0)
+        out_cap = total;
     if (nseg >= (int64_t)INT32_MAX)
         return fail(RTREE_EOVERFLOW, "too many segments to sort (%lld)", (long long)nseg);
     // Every list length stays on the device; the launches below are sized
@@ -1045,7 +1047,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
             blocks = (int64_t)sms * 16;
         KernelTimer kt_("sort_classify", s);
         k_classify<<<(unsigned)blocks, 256, 0, s>>>(offsets, nseg, lists.p, nseg, large_tmp.p, hdr.p,
-                                                    S, out, total);
+                                                    S, out, out_cap);
         RT_LAUNCH();
     }
     auto L = [&](int c) { return lists.p + (int64_t)c * nseg; };

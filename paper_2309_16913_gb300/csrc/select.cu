@@ -33,6 +33,8 @@
 //   DESC     writes the leaf hits and, for every whole subtree, its (lo, hi)
 //            range of the tree's id array; the sorted output is then built
 //            by the segmented sort, which reads the ranges directly.
+#include <cstring>
+
 #include "internal.cuh"
 
 namespace rt {
@@ -749,6 +751,197 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     res->total = total;
     res->offsets = off.release();
     res->ids = ids.release();
+    return RTREE_OK;
+}
+
+// Host-result form.  One count pass over the batch fixes every query's
+// offset; the offsets come back to the host first, which both answers the
+// caller and cuts the batch into chunks of about equal id counts.  Each
+// chunk's second pass (descriptors, then the segmented sort; or the scatter
+// pass unsorted) runs on `s`, and when it is done its ids are copied to the
+// caller's buffer on a second stream while the next chunk runs.
+rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
+                               int mapping, int order, cudaStream_t s, int64_t *h_off, int32_t *h_ids,
+                               int64_t capacity, int64_t *h_total)
+{
+    constexpr int kChunks = 8;
+    *h_total = 0;
+    if (Q == 0 || t->nodes == 0) {
+        memset(h_off, 0, (size_t)(Q + 1) * sizeof(int64_t));
+        return RTREE_OK;
+    }
+    if (!pick(t->fanout, t->layout, PASS_COUNT))
+        return fail(RTREE_EINVAL, "unsupported fanout %d", t->fanout);
+    const bool wq = mapping == RTREE_MAP_WORK_QUEUE;
+    DevBuf<int32_t> cnt(s), cnt_leaf(s), cnt_rng(s), flags(s);
+    DevBuf<unsigned long long> ctr(s);
+    DevBuf<int64_t> off(s), off_leaf(s), off_rng(s);
+    DevBuf<uint32_t> perm(s);
+    RT_TRY(cnt.alloc(Q, "select counts"));
+    RT_TRY(off.alloc(Q + 1, "select offsets"));
+    RT_TRY(flags.alloc(2, "select flags"));
+    RT_TRY(ctr.alloc(1 + kChunks, "select work counters"));
+    RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
+    RT_CUDA(cudaMemsetAsync(ctr.p, 0, (1 + kChunks) * sizeof(unsigned long long), s));
+    if (order == RTREE_ORDER_HILBERT) {
+        RT_TRY(perm.alloc(Q, "query order"));
+        RT_TRY(hilbert_order(t, queries, Q, perm.p, s));
+    }
+    SelIO io = unlimited();
+    io.counts = cnt.p;
+    io.order = perm.p;
+    if (sorted) {
+        RT_TRY(cnt_leaf.alloc(Q, "select counts"));
+        RT_TRY(cnt_rng.alloc(Q, "select counts"));
+        RT_TRY(off_leaf.alloc(Q + 1, "select offsets"));
+        RT_TRY(off_rng.alloc(Q + 1, "select offsets"));
+        io.counts_leaf = cnt_leaf.p;
+        io.counts_rng = cnt_rng.p;
+    }
+    if (wq) {
+        RT_CUDA(cudaMemsetAsync(cnt.p, 0, Q * sizeof(int32_t), s));
+        if (sorted) {
+            RT_CUDA(cudaMemsetAsync(cnt_leaf.p, 0, Q * sizeof(int32_t), s));
+            RT_CUDA(cudaMemsetAsync(cnt_rng.p, 0, Q * sizeof(int32_t), s));
+        }
+        RT_TRY(launch_wq(PASS_COUNT, t, queries, Q, io, flags.p, s));
+    } else {
+        RT_TRY(launch(PASS_COUNT, t, queries, Q, io, ctr.p, flags.p, s));
+    }
+    RT_TRY(scan_exclusive(cnt.p, off.p, Q, s));
+    if (sorted) {
+        RT_TRY(scan_exclusive(cnt_leaf.p, off_leaf.p, Q, s));
+        RT_TRY(scan_exclusive(cnt_rng.p, off_rng.p, Q, s));
+    }
+    int64_t h[2] = {0, 0};
+    int32_t hflags = 0;
+    RT_CUDA(cudaMemcpyAsync(h_off, off.p, (Q + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (sorted) {
+        RT_CUDA(cudaMemcpyAsync(&h[0], off_leaf.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RT_CUDA(cudaMemcpyAsync(&h[1], off_rng.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
+    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (hflags & FLAG_TIMEOUT)
+        return fail(RTREE_ETIMEOUT, "select count pass: a work-queue wait exceeded its limit");
+    if (hflags)
+        return fail(RTREE_EINTERNAL, "select count pass reported device flags 0x%x", hflags);
+    const int64_t total = h_off[Q];
+    *h_total = total;
+    if (total > capacity)
+        return fail(RTREE_EOVERFLOW, "rtree_range_select_host: %lld ids, capacity %lld",
+                    (long long)total, (long long)capacity);
+    if (total == 0)
+        return RTREE_OK;
+
+    DevBuf<int32_t> ids(s), cursors(s), leaf(s);
+    DevBuf<int2> rng(s);
+    DevBuf<uint32_t> cperm(s);
+    RT_TRY(ids.alloc(total, "select ids"));
+    if (sorted) {
+        RT_TRY(leaf.alloc(h[0], "select leaf hits"));
+        RT_TRY(rng.alloc(h[1], "select whole subtrees"));
+    }
+    if (wq) {
+        RT_TRY(cursors.alloc(2 * Q, "select cursors"));
+        RT_CUDA(cudaMemsetAsync(cursors.p, 0, 2 * Q * sizeof(int32_t), s));
+    }
+    // chunk boundaries: query c_k is the first whose ids start at or after k*total/kChunks
+    int64_t bound[kChunks + 1];
+    bound[0] = 0;
+    for (int k = 1; k < kChunks; ++k) {
+        const int64_t want = total / kChunks * k;
+        int64_t lo = bound[k - 1], hi = Q;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (h_off[mid] < want)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        bound[k] = lo;
+    }
+    bound[kChunks] = Q;
+    int64_t max_chunk = 0;
+    for (int k = 0; k < kChunks; ++k)
+        max_chunk = bound[k + 1] - bound[k] > max_chunk ? bound[k + 1] - bound[k] : max_chunk;
+    if (order == RTREE_ORDER_HILBERT)
+        RT_TRY(cperm.alloc(max_chunk, "query order"));
+
+    struct CopyStream {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev[kChunks] = {};
+        ~CopyStream()
+        {
+            if (cs) {
+                cudaStreamSynchronize(cs);
+                cudaStreamDestroy(cs);
+            }
+            for (auto e : ev)
+                if (e)
+                    cudaEventDestroy(e);
+        }
+    } cp;
+    RT_CUDA(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
+    for (int k = 0; k < kChunks; ++k)
+        RT_CUDA(cudaEventCreateWithFlags(&cp.ev[k], cudaEventDisableTiming));
+    for (int k = 0; k < kChunks; ++k) {
+        const int64_t c0 = bound[k], qc = bound[k + 1] - bound[k];
+        if (qc == 0)
+            continue;
+        const float4 *qk = queries + c0;
+        SelIO so = unlimited();
+        if (order == RTREE_ORDER_HILBERT) {
+            RT_TRY(hilbert_order(t, qk, qc, cperm.p, s));
+            so.order = cperm.p;
+        }
+        if (!sorted) {
+            so.offsets = off.p + c0;
+            so.out = ids.p;
+            if (wq) {
+                so.cur_ids = cursors.p + c0;
+                RT_TRY(launch_wq(PASS_SCATTER, t, qk, qc, so, flags.p, s));
+            } else {
+                RT_TRY(launch(PASS_SCATTER, t, qk, qc, so, ctr.p + 1 + k, flags.p, s));
+            }
+        } else {
+            so.off_leaf = off_leaf.p + c0;
+            so.off_rng = off_rng.p + c0;
+            so.leaf_out = leaf.p;
+            so.rng_out = rng.p;
+            if (wq) {
+                so.cur_leaf = cursors.p + c0;
+                so.cur_rng = cursors.p + Q + c0;
+                RT_TRY(launch_wq(PASS_DESC, t, qk, qc, so, flags.p, s));
+            } else {
+                RT_TRY(launch(PASS_DESC, t, qk, qc, so, ctr.p + 1 + k, flags.p, s));
+            }
+            SortSources src{};
+            src.leaf = leaf.p;
+            src.off_leaf = off_leaf.p + c0;
+            src.rng = rng.p;
+            src.off_rng = off_rng.p + c0;
+            src.tree_ids = t->ids;
+            RT_TRY(segmented_sort_gather(ids.p, off.p + c0, qc, h_off[c0 + qc] - h_off[c0], src, s,
+                                         flags.p + 1, total));
+        }
+        const int64_t a = h_off[c0], b = h_off[c0 + qc];
+        RT_CUDA(cudaEventRecord(cp.ev[k], s));
+        RT_CUDA(cudaStreamWaitEvent(cp.cs, cp.ev[k], 0));
+        if (b > a)
+            RT_CUDA(cudaMemcpyAsync(h_ids + a, ids.p + a, (b - a) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                    cp.cs));
+    }
+    int32_t hf2[2] = {0, 0};
+    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    RT_CUDA(cudaStreamSynchronize(cp.cs));
+    if (hf2[1])
+        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
+    if (hf2[0] & FLAG_TIMEOUT)
+        return fail(RTREE_ETIMEOUT, "select second pass: a work-queue wait exceeded its limit");
+    if (hf2[0])
+        return fail(RTREE_EINTERNAL, "select second pass reported device flags 0x%x", hf2[0]);
     return RTREE_OK;
 }
 

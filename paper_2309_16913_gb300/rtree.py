@@ -106,6 +106,8 @@ def _bind(lib):
         "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
         "rtree_join_ex": (C.c_int, [vp, vp, vp, vp, C.POINTER(vp)]),
         "rtree_save": (C.c_int, [vp, C.c_char_p, vp]),
+        "rtree_range_select_host": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64,
+                                              C.POINTER(C.c_int64)]),
         "rtree_load": (C.c_int, [C.c_char_p, C.c_int, vp, C.POINTER(vp)]),
         "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
         "rtree_range_select_noalloc": (C.c_int, [vp, vp, i64, vp, vp, i64, C.POINTER(C.c_int64), vp]),
@@ -293,6 +295,36 @@ def rtree_range_select(handle: int, queries, unsorted: bool = False, mapping: st
     _check(lib.rtree_range_select(handle, qp, q, C.byref(opts), _stream(stream), C.byref(out)), lib)
     del keep
     return out.value
+
+
+def rtree_range_select_host(handle: int, queries, offsets, ids, unsorted: bool = False,
+                            mapping: str | int = "auto", order: str | int = "input", stream=None) -> int:
+    """Select into host arrays (NumPy or CPU tensors; pinned memory overlaps
+    the copies with the work).  ``offsets`` int64[q+1], ``ids`` int32
+    [capacity].  Returns the total; raises RTreeError (RTREE_EOVERFLOW) when
+    ids is too small, after offsets have been written."""
+    lib = load_library()
+    qp, q, keep = _as_rows(queries, "queries")
+    opts = rtree_select_opts_t()
+    opts.unsorted = 1 if unsorted else 0
+    opts.mapping = MAPPINGS[mapping] if isinstance(mapping, str) else int(mapping)
+    opts.order = ORDERS[order] if isinstance(order, str) else int(order)
+
+    def host_ptr(a, dtype, name):
+        if _is_torch(a):
+            assert not a.is_cuda and a.is_contiguous(), f"{name} must be a contiguous CPU tensor"
+            return a.data_ptr(), a.numel()
+        assert a.dtype == dtype and a.flags["C_CONTIGUOUS"], f"{name} must be contiguous {dtype}"
+        return a.ctypes.data, a.size
+    op, on = host_ptr(offsets, np.int64, "offsets")
+    ip, cap = host_ptr(ids, np.int32, "ids")
+    assert on >= q + 1, "offsets needs q+1 entries"
+    total = C.c_int64()
+    rc = lib.rtree_range_select_host(handle, qp, q, C.byref(opts), _stream(stream), op, ip if cap else None,
+                                     cap, C.byref(total))
+    del keep
+    _check(rc, lib)
+    return total.value
 
 
 def rtree_range_select_noalloc(handle: int, queries, offsets, ids, stream=None) -> int:
