@@ -348,7 +348,8 @@ RTREE_API rtree_status rtree_range_select_stats(const rtree_t *tree, const float
  * rtree_range_select_host -- rtree_range_select with the result written to
  * caller-owned host memory, the copy overlapped with the work.  One count
  * pass over the batch fixes every query's offset (written to `offsets`
- * first); the batch is then cut into chunks of about equal id counts, and
+ * first); the batch is then cut into chunks of about equal id counts (about
+ * 128M ids each, at most 32), and
  * while the second pass and sort of one chunk run on `stream`, the ids of
  * the chunk before are copied to `ids` on a second stream.  Same ids, order
  * and options as rtree_range_select.

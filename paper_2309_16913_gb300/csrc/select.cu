@@ -759,12 +759,15 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
 // caller and cuts the batch into chunks of about equal id counts.  Each
 // chunk's second pass (descriptors, then the segmented sort; or the scatter
 // pass unsorted) runs on `s`, and when it is done its ids are copied to the
-// caller's buffer on a second stream while the next chunk runs.
+// caller's buffer on a second stream while the next chunk runs.  Chunks of
+// about 128M ids (at most 32 of them) balance the exposed ends (the first
+// chunk's select, the last chunk's copy) against per-chunk launch costs.
 rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
                                int mapping, int order, cudaStream_t s, int64_t *h_off, int32_t *h_ids,
                                int64_t capacity, int64_t *h_total)
 {
-    constexpr int kChunks = 8;
+    constexpr int kMaxChunks = 32;
+    constexpr int64_t kChunkIds = int64_t(128) << 20;
     *h_total = 0;
     if (Q == 0 || t->nodes == 0) {
         memset(h_off, 0, (size_t)(Q + 1) * sizeof(int64_t));
@@ -780,9 +783,9 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
     RT_TRY(cnt.alloc(Q, "select counts"));
     RT_TRY(off.alloc(Q + 1, "select offsets"));
     RT_TRY(flags.alloc(2, "select flags"));
-    RT_TRY(ctr.alloc(1 + kChunks, "select work counters"));
+    RT_TRY(ctr.alloc(1 + kMaxChunks, "select work counters"));
     RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
-    RT_CUDA(cudaMemsetAsync(ctr.p, 0, (1 + kChunks) * sizeof(unsigned long long), s));
+    RT_CUDA(cudaMemsetAsync(ctr.p, 0, (1 + kMaxChunks) * sizeof(unsigned long long), s));
     if (order == RTREE_ORDER_HILBERT) {
         RT_TRY(perm.alloc(Q, "query order"));
         RT_TRY(hilbert_order(t, queries, Q, perm.p, s));
@@ -846,8 +849,14 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
         RT_TRY(cursors.alloc(2 * Q, "select cursors"));
         RT_CUDA(cudaMemsetAsync(cursors.p, 0, 2 * Q * sizeof(int32_t), s));
     }
-    // chunk boundaries: query c_k is the first whose ids start at or after k*total/kChunks
-    int64_t bound[kChunks + 1];
+    // chunk boundaries: query c_k is the first whose ids start at or after k*total/nchunks
+    int64_t nc64 = total / kChunkIds + 1;
+    if (nc64 > kMaxChunks)
+        nc64 = kMaxChunks;
+    if (nc64 > Q)
+        nc64 = Q;
+    const int kChunks = (int)nc64;
+    int64_t bound[kMaxChunks + 1];
     bound[0] = 0;
     for (int k = 1; k < kChunks; ++k) {
         const int64_t want = total / kChunks * k;
@@ -870,7 +879,7 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
 
     struct CopyStream {
         cudaStream_t cs = nullptr;
-        cudaEvent_t ev[kChunks] = {};
+        cudaEvent_t ev[kMaxChunks] = {};
         ~CopyStream()
         {
             if (cs) {
