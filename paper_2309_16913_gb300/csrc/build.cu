@@ -72,11 +72,12 @@ __global__ void k_keys(const float4 *__restrict__ boxes, int64_t m, int axis,
 __global__ void k_slab_of(const uint32_t *__restrict__ order_x, int64_t m, int64_t cap,
                           uint32_t *__restrict__ slab)
 {
+    const uint32_t cap32 = (uint32_t)cap;  // m < 2^31, so ranks and cap fit 32 bits
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m;
          r += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = order_x[r];
         if (i < m)
-            slab[i] = (uint32_t)(r / cap);
+            slab[i] = (uint32_t)r / cap32;
     }
 }
 
@@ -91,25 +92,41 @@ __global__ void k_gather_slab(const uint32_t *__restrict__ order_y,
     }
 }
 
-// Bounding box of each packed node (exact min/max).
+// Bounding box of each packed node (exact min/max).  A group of G = min(F,
+// 32) lanes takes one node: each lane reduces every G-th item, then the
+// group reduces by shuffles (min/max are exact in any order).
 __global__ void k_node_boxes(const float4 *__restrict__ items, const uint32_t *__restrict__ pack,
                              int64_t m, int F, int64_t P, float4 *__restrict__ out)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = k * F, hi = min(m, lo + F);
+    const int G = F < 32 ? F : 32;
+    const int lane = threadIdx.x & 31, sub = lane % G;
+    const int64_t group = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    const int64_t rounds = (P + groups - 1) / groups;  // the same count for every lane
+    for (int64_t t = 0; t < rounds; ++t) {
+        const int64_t k = group + t * groups;
         float4 acc = empty_box();
-        for (int64_t r = lo; r < hi; ++r) {
-            const uint32_t it = pack[r];
-            if (it >= m)
-                continue;
-            const float4 b = items[it];
-            acc.x = fminf(acc.x, b.x);
-            acc.y = fminf(acc.y, b.y);
-            acc.z = fmaxf(acc.z, b.z);
-            acc.w = fmaxf(acc.w, b.w);
+        if (k < P) {
+            const int64_t lo = k * F, hi = min(m, lo + F);
+            for (int64_t r = lo + sub; r < hi; r += G) {
+                const uint32_t it = pack[r];
+                if (it >= m)
+                    continue;
+                const float4 b = items[it];
+                acc.x = fminf(acc.x, b.x);
+                acc.y = fminf(acc.y, b.y);
+                acc.z = fmaxf(acc.z, b.z);
+                acc.w = fmaxf(acc.w, b.w);
+            }
         }
-        out[k] = acc;
+        for (int d = G >> 1; d > 0; d >>= 1) {
+            acc.x = fminf(acc.x, __shfl_xor_sync(RT_FULL, acc.x, d));
+            acc.y = fminf(acc.y, __shfl_xor_sync(RT_FULL, acc.y, d));
+            acc.z = fmaxf(acc.z, __shfl_xor_sync(RT_FULL, acc.z, d));
+            acc.w = fmaxf(acc.w, __shfl_xor_sync(RT_FULL, acc.w, d));
+        }
+        if (k < P && sub == 0)
+            out[k] = acc;
     }
 }
 
@@ -186,10 +203,11 @@ __global__ void k_layout(int F, int layout, int64_t P, int64_t m,
 {
     const int64_t last_cnt = m - (P - 1) * F;
     const int64_t pp = *partial_pos;
+    const int logF = __ffs(F) - 1;  // F is a power of two
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < P * F;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = idx / F;
-        const int j = (int)(idx % F);
+        const int64_t s = idx >> logF;
+        const int j = (int)(idx & (F - 1));
         const int64_t o = order[s];
         const int64_t cnt = (o == P - 1) ? last_cnt : F;
         const int64_t first = s * F - (s > pp ? (F - last_cnt) : 0);
@@ -381,7 +399,7 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
             RT_TRY(nb->alloc(P, "node boxes"));
             {
                 KernelTimer kt_("node_boxes", s);
-                k_node_boxes<<<blocks_for(P), kThreads, 0, s>>>(cur, pack->p, m, F, P, nb->p);
+                k_node_boxes<<<blocks_for(P * (F < 32 ? F : 32)), kThreads, 0, s>>>(cur, pack->p, m, F, P, nb->p);
                 RT_LAUNCH();
             }
             m_of.push_back(m);
