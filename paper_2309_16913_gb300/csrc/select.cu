@@ -65,9 +65,9 @@ __device__ __forceinline__ void warp_copy(int32_t *__restrict__ out,
 
 // Results of one walk (a query, or one (query, subtree) work item).
 struct Walk {
-    int64_t cur;   // ids found, warp-uniform
-    int64_t lcur;  // of which found one by one in leaves
-    int64_t rcur;  // whole subtrees taken
+    int32_t cur;   // ids found, warp-uniform (a query's ids fit 31 bits)
+    int32_t lcur;  // of which found one by one in leaves
+    int32_t rcur;  // whole subtrees taken
     unsigned long long n_visit, n_leaf;
     bool overflow;
 };
@@ -116,6 +116,32 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         b[c] = node >= 0 ? load_entry_t<F, LAYOUT>(t.mbr, node, sub + c * G) : empty_box();
     const int4 m = node >= 0 ? __ldg(t.meta + node) : make_int4(0, 0, 0, 0);
     const bool leaf = node >= t.leaf_base;
+    if (K == 1 && leaf) {
+        // One node per warp step and it is a leaf (warp-uniform): only the
+        // overlap test and the emit are needed.
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int j = sub + c * G;
+            const bool emit = j < m.y && meets(b[c], q);
+            const unsigned me = __ballot_sync(RT_FULL, emit);
+            if (PASS == PASS_SCATTER && me) {
+                const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, __popc(me), lane) : sg.base + wk.cur;
+                const int64_t o = at + __popc(me & lt);
+                if (emit && o < sg.lim && o < io.out_cap)
+                    io.out[o] = __ldg(t.ids + m.x + j);
+            }
+            if (PASS == PASS_DESC && me) {
+                const int64_t at = WQ ? sg.lbase + reserve(io.cur_leaf + qi, __popc(me), lane) : sg.lbase + wk.lcur;
+                const int64_t o = at + __popc(me & lt);
+                if (emit && o < sg.llim && o < io.leaf_cap)
+                    io.leaf_out[o] = __ldg(t.ids + m.x + j);
+            }
+            wk.cur += __popc(me);
+            wk.lcur += __popc(me);
+        }
+        __syncwarp();
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int j = sub + c * G;
