@@ -116,9 +116,12 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         b[c] = node >= 0 ? load_entry_t<F, LAYOUT>(t.mbr, node, sub + c * G) : empty_box();
     const int4 m = node >= 0 ? __ldg(t.meta + node) : make_int4(0, 0, 0, 0);
     const bool leaf = node >= t.leaf_base;
-    if (K == 1 && leaf) {
-        // One node per warp step and it is a leaf (warp-uniform): only the
-        // overlap test and the emit are needed.
+    // Every node of this step is a leaf (warp-uniform; with K == 1 there is
+    // one node): only the overlap test and the emit are needed.  Lanes
+    // without a node see count 0.
+    const bool all_leaf = K == 1 ? leaf : __all_sync(RT_FULL, node < 0 || leaf);
+    const bool any_leaf = K == 1 ? leaf : __any_sync(RT_FULL, node >= 0 && leaf);
+    if (all_leaf) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int j = sub + c * G;
@@ -156,21 +159,23 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
                 st[pos] = m.x + j;
         }
         top += __popc(mp);
-        const unsigned me = __ballot_sync(RT_FULL, emit);
-        if (PASS == PASS_SCATTER && me) {
-            const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, __popc(me), lane) : sg.base + wk.cur;
-            const int64_t o = at + __popc(me & lt);
-            if (emit && o < sg.lim && o < io.out_cap)
-                io.out[o] = __ldg(t.ids + m.x + j);
+        if (any_leaf) {  // a step of internal nodes only emits nothing
+            const unsigned me = __ballot_sync(RT_FULL, emit);
+            if (PASS == PASS_SCATTER && me) {
+                const int64_t at = WQ ? sg.base + reserve(io.cur_ids + qi, __popc(me), lane) : sg.base + wk.cur;
+                const int64_t o = at + __popc(me & lt);
+                if (emit && o < sg.lim && o < io.out_cap)
+                    io.out[o] = __ldg(t.ids + m.x + j);
+            }
+            if (PASS == PASS_DESC && me) {
+                const int64_t at = WQ ? sg.lbase + reserve(io.cur_leaf + qi, __popc(me), lane) : sg.lbase + wk.lcur;
+                const int64_t o = at + __popc(me & lt);
+                if (emit && o < sg.llim && o < io.leaf_cap)
+                    io.leaf_out[o] = __ldg(t.ids + m.x + j);
+            }
+            wk.cur += __popc(me);
+            wk.lcur += __popc(me);
         }
-        if (PASS == PASS_DESC && me) {
-            const int64_t at = WQ ? sg.lbase + reserve(io.cur_leaf + qi, __popc(me), lane) : sg.lbase + wk.lcur;
-            const int64_t o = at + __popc(me & lt);
-            if (emit && o < sg.llim && o < io.leaf_cap)
-                io.leaf_out[o] = __ldg(t.ids + m.x + j);
-        }
-        wk.cur += __popc(me);
-        wk.lcur += __popc(me);
         const unsigned mc = __ballot_sync(RT_FULL, cont);
         if (mc) {
             int lo = 0, hi = 0;
