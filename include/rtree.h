@@ -342,7 +342,9 @@ RTREE_API rtree_status rtree_range_select_stats(const rtree_t *tree, const float
  * every outer child's MBR is broadcast to all lanes and compared with the
  * inner children held one per lane (the one-to-many comparison of Section
  * 4.1).  The trees may have different fanouts and layouts but must be on the
- * same device.  Errors: RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA.
+ * same device.  A join returns at most 2^31-1 pairs (the pair sort is a
+ * 32-bit-indexed radix sort); a larger result is RTREE_EOVERFLOW.
+ * Errors: RTREE_EINVAL, RTREE_ENOMEM, RTREE_ECUDA, RTREE_EOVERFLOW.
  */
 /*
  * rtree_range_select_host -- rtree_range_select with the result written to

@@ -66,3 +66,21 @@ def test_beyond_32_bit_sizes(rt, data):
                 assert np.array_equal(got, brute(data, q[i])), i
         finally:
             res.close()
+
+
+def test_join_beyond_pair_limit_reports_overflow(rt):
+    """50k x 50k rectangles that all overlap: 2.5e9 pairs, past the 2^31-1
+    pairs a join can return; the call must fail cleanly and the library
+    must keep working."""
+    g = dg.rng_for(91)
+    a = np.concatenate([g.random((50_000, 2)) * 0.1, 0.9 + g.random((50_000, 2)) * 0.1], axis=1).astype(np.float32)
+    b = np.concatenate([g.random((50_000, 2)) * 0.1, 0.9 + g.random((50_000, 2)) * 0.1], axis=1).astype(np.float32)
+    with rt.RTree(a, None, fanout=32) as ta, rt.RTree(b, None, fanout=32) as tb:
+        with pytest.raises(rt.RTreeError) as e:
+            ta.join(tb)
+        assert e.value.status == rt.RTREE_EOVERFLOW
+        small = rt.RTree(a[:100], None, fanout=32)
+        res = small.join(tb)
+        assert res.total == 100 * 50_000  # still works
+        res.close()
+        small.close()
