@@ -181,6 +181,107 @@ __global__ void k_sort_children(const float4 *__restrict__ items, uint32_t *__re
     }
 }
 
+// ---- small levels: one CTA builds every level of at most kSmallLevel items
+// (the upper levels of a big tree, or all of a small one), instead of a
+// dozen launches per level.  Each level is sorted twice in shared memory by
+// a bitonic network over 64-bit composite keys that end in the item index,
+// which gives exactly the stable orders of the radix path:
+//   (x centre key, item)  -> slab = rank / (S*F),
+//   (slab, y centre key, item) -> the packing order.
+constexpr int kSmallLevel = 4096;  // item indices fit 12 bits
+
+struct SmallLevels {
+    int count;                      // levels to build, bottom up
+    int sort_children;
+    int64_t m[RT_MAX_LEVELS];       // items of each level
+    uint32_t *pack[RT_MAX_LEVELS];  // packing order of each level
+    float4 *box[RT_MAX_LEVELS];     // node boxes of each level (items of the next)
+};
+
+__device__ __forceinline__ void block_bitonic_u64(unsigned long long *key, int M)
+{
+    for (int size = 2; size <= M; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (M >> 1); i += blockDim.x) {
+                const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_build_small(const float4 *__restrict__ items0, int F,
+                                                       SmallLevels L)
+{
+    __shared__ unsigned long long key[kSmallLevel];
+    __shared__ uint32_t aux[kSmallLevel];  // slab of each item; then a node's reordered items
+    for (int l = 0; l < L.count; ++l) {
+        const float4 *it = l == 0 ? items0 : L.box[l - 1];
+        const int m = (int)L.m[l];
+        const int P = (m + F - 1) / F;
+        int S = (int)sqrtf((float)P);
+        while (S * S < P)
+            ++S;
+        while (S > 1 && (S - 1) * (S - 1) >= P)
+            --S;
+        const int cap = S * F;
+        int M = 1;
+        while (M < m)
+            M <<= 1;
+        for (int i = threadIdx.x; i < M; i += blockDim.x)
+            key[i] = i < m ? ((unsigned long long)centre_key(it[i].x, it[i].z) << 32) | (unsigned)i : ~0ull;
+        __syncthreads();
+        block_bitonic_u64(key, M);
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            aux[key[r] & 0xfffu] = (uint32_t)(r / cap);
+        __syncthreads();
+        for (int i = threadIdx.x; i < M; i += blockDim.x)
+            key[i] = i < m ? ((unsigned long long)aux[i] << 44) |
+                                 ((unsigned long long)centre_key(it[i].y, it[i].w) << 12) | (unsigned)i
+                           : ~0ull;
+        __syncthreads();
+        block_bitonic_u64(key, M);
+        uint32_t *pack = L.pack[l];
+        if (L.sort_children) {  // each node's items by ascending lx, ties in packing order
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                const int lo = r / F * F, hi = min(m, lo + F);
+                const uint32_t item = (uint32_t)(key[r] & 0xfffu);
+                const float x = it[item].x;
+                int rank = 0;
+                for (int j = lo; j < hi; ++j) {
+                    const float v = it[key[j] & 0xfffu].x;
+                    rank += (v < x) || (v == x && j < r);
+                }
+                aux[lo + rank] = item;
+            }
+        } else {
+            for (int r = threadIdx.x; r < m; r += blockDim.x)
+                aux[r] = (uint32_t)(key[r] & 0xfffu);
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            pack[r] = aux[r];
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+            float4 acc = empty_box();
+            for (int r = k * F; r < min(m, k * F + F); ++r) {
+                const float4 b = it[aux[r]];
+                acc.x = fminf(acc.x, b.x);
+                acc.y = fminf(acc.y, b.y);
+                acc.z = fmaxf(acc.z, b.z);
+                acc.w = fmaxf(acc.w, b.w);
+            }
+            L.box[l][k] = acc;
+        }
+        __syncthreads();  // the next level reads these boxes
+    }
+}
+
 __global__ void k_find_partial(const uint32_t *__restrict__ order, int64_t P,
                                int64_t *__restrict__ pos)
 {
@@ -349,6 +450,34 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
         for (;;) {
             if ((int)m_of.size() >= RT_MAX_LEVELS)
                 return fail(RTREE_EOVERFLOW, "tree would exceed %d levels", RT_MAX_LEVELS);
+            if (m <= kSmallLevel) {  // this level and all above it in one CTA
+                SmallLevels L{};
+                L.sort_children = sort_children ? 1 : 0;
+                for (int64_t mm = m;;) {
+                    if ((int)m_of.size() >= RT_MAX_LEVELS)
+                        return fail(RTREE_EOVERFLOW, "tree would exceed %d levels", RT_MAX_LEVELS);
+                    const int64_t P = (mm + F - 1) / F;
+                    auto *pk = new DevBuf<uint32_t>(s);
+                    packs.push_back(pk);
+                    RT_TRY(pk->alloc(mm, "build packing order"));
+                    auto *bx = new DevBuf<float4>(s);
+                    boxes.push_back(bx);
+                    RT_TRY(bx->alloc(P, "node boxes"));
+                    L.m[L.count] = mm;
+                    L.pack[L.count] = pk->p;
+                    L.box[L.count] = bx->p;
+                    ++L.count;
+                    m_of.push_back(mm);
+                    p_of.push_back(P);
+                    if (P == 1)
+                        break;
+                    mm = P;
+                }
+                KernelTimer kt_("build_small", s);
+                k_build_small<<<1, 1024, 0, s>>>(cur, F, L);
+                RT_LAUNCH();
+                break;
+            }
             const int64_t P = (m + F - 1) / F;
             const int64_t S = ceil_sqrt(P);
             const int64_t cap = S * F;
