@@ -8,7 +8,7 @@
 //                 on 1-8 keys per lane in registers (shuffles across lanes,
 //                 swaps inside a lane);
 //   257..16384    one CTA of 128-1024 threads, entirely in shared memory:
-//                 bucket the keys by their top differing bits (2-4 keys per
+//                 bucket the keys by value within their range (1-4 keys per
 //                 bucket for spread-out ids) with shared atomics, then each
 //                 thread sorts whole buckets in registers with a bitonic
 //                 network; a crowded bucket sends the segment to a stable
@@ -33,7 +33,7 @@ constexpr int kItems = 16;              // keys per thread in the CTA sort
 constexpr int kCtaMax = 1024 * kItems;  // 16384: largest in-shared-memory segment
 constexpr uint32_t kSign = 0x80000000u;
 constexpr int kBucketBitsMax = 12;      // at most 4096 buckets
-constexpr int kBucketDensity = 2;       // buckets = 2^(ceil(log2 n) - 2): 2-4 keys each
+constexpr int kBucketDensity = 1;       // 2^(ceil(log2 n) - 1) buckets of the key range
 constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to LSD
 
 // Segment classes (index into the class lists).
@@ -245,7 +245,7 @@ struct CtaSmem {
         };
     };
     uint32_t wsum[W];
-    uint32_t red_and[W], red_or[W];
+    uint32_t red0[W], red1[W];  // per-warp partial reductions
     uint32_t crowded;
 };
 
@@ -347,18 +347,40 @@ __device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_
         a_or |= __shfl_xor_sync(RT_FULL, a_or, d);
     }
     if (lane == 0) {
-        sm.red_and[w] = a_and;
-        sm.red_or[w] = a_or;
+        sm.red0[w] = a_and;
+        sm.red1[w] = a_or;
     }
     __syncthreads();
     a_and = 0xffffffffu;
     a_or = 0;
     for (int x = 0; x < W; ++x) {
-        a_and &= sm.red_and[x];
-        a_or |= sm.red_or[x];
+        a_and &= sm.red0[x];
+        a_or |= sm.red1[x];
     }
     __syncthreads();
     return a_and ^ a_or;
+}
+
+// Block-wide minimum and maximum of the keys; every thread gets both.
+template <int THREADS>
+__device__ __forceinline__ void block_minmax(CtaSmem<THREADS> &sm, uint32_t &kmin, uint32_t &kmax)
+{
+    constexpr int W = THREADS / 32;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    kmin = __reduce_min_sync(RT_FULL, kmin);
+    kmax = __reduce_max_sync(RT_FULL, kmax);
+    if (lane == 0) {
+        sm.red0[w] = kmin;
+        sm.red1[w] = kmax;
+    }
+    __syncthreads();
+    kmin = 0xffffffffu;
+    kmax = 0;
+    for (int x = 0; x < W; ++x) {
+        kmin = min(kmin, sm.red0[x]);
+        kmax = max(kmax, sm.red1[x]);
+    }
+    __syncthreads();
 }
 
 // Sorts buf[s0 .. s0+c), c <= N, in registers: a bitonic network over N
@@ -394,9 +416,12 @@ __device__ __forceinline__ void bucket_network(uint32_t *buf, int s0, int c)
 }
 
 // Sorts the n <= THREADS*kItems keys in sm.buf and writes them to dst (xor
-// kSign back to ids).  Keys are bucketed by their top B differing bits (B =
-// ceil(log2 n) - 2, at most 12) with shared atomics, so a bucket holds two to
-// four keys on average; each bucket is then sorted in registers.
+// kSign back to ids).  Keys are bucketed by value, (key - min) >> shift with
+// B = ceil(log2 n) - 1 bits (at most 12) of the key range, using shared
+// atomics, so a bucket of spread-out keys holds one to four keys; each
+// bucket is then sorted in registers.  Measuring from the minimum keeps a
+// range that straddles a power of two (e.g. ids around 2^k, or of both
+// signs) from crowding into a few buckets.
 // Returns false, having written the unsorted ids to dst, if a bucket holds
 // more than kBucketCrowded keys (the caller then sorts dst with LSD).
 template <int THREADS>
@@ -404,7 +429,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
                                                 int n)
 {
     uint32_t key[kItems];
-    uint32_t a_and = 0xffffffffu, a_or = 0;
+    uint32_t kmin = 0xffffffffu, kmax = 0;
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (i * THREADS >= n)
@@ -413,25 +438,27 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         key[i] = 0;
         if (p < n) {
             key[i] = sm.buf[p];
-            a_and &= key[i];
-            a_or |= key[i];
+            kmin = min(kmin, key[i]);
+            kmax = max(kmax, key[i]);
         }
     }
-    const uint32_t diff = block_diff<THREADS>(sm, a_and, a_or);
-    if (diff == 0) {  // all keys equal
+    block_minmax<THREADS>(sm, kmin, kmax);
+    if (kmin == kmax) {  // all keys equal
         for (int p = threadIdx.x; p < n; p += THREADS)
             dst[p] = (int32_t)(sm.buf[p] ^ kSign);
         __syncthreads();
         return true;
     }
-    const int hb = 31 - __clz(diff);
+    // bucket = (key - kmin) >> shift: B = ceil(log2 n) - 1 bits (at most 12)
+    // of the key range, so only buckets inside [kmin, kmax] exist
+    const uint32_t span = kmax - kmin;
+    const int width = 32 - __clz(span);
     int bits = (32 - __clz((unsigned)(n - 1))) - kBucketDensity;
     bits = bits < 1 ? 1 : (bits > kBucketBitsMax ? kBucketBitsMax : bits);
-    if (bits > hb + 1)
-        bits = hb + 1;
-    const int shift = hb + 1 - bits;
-    const int nb = 1 << bits;
-    const uint32_t mask = (uint32_t)nb - 1u;
+    if (bits > width)
+        bits = width;
+    const int shift = width - bits;
+    const int nb = (int)(span >> shift) + 1;
     for (int b = threadIdx.x; b < nb; b += THREADS)
         sm.cnt[b] = 0;
     if (threadIdx.x == 0)
@@ -442,7 +469,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         if (i * THREADS >= n)
             break;
         if (i * THREADS + threadIdx.x < n)
-            atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
+            atomicAdd(&sm.cnt[(key[i] - kmin) >> shift], 1u);
     }
     __syncthreads();
     {  // exclusive scan of the nb counts: each thread owns a run of them
@@ -473,7 +500,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         if (i * THREADS >= n)
             break;
         if (i * THREADS + threadIdx.x < n) {
-            const uint32_t pos = atomicAdd(&sm.cnt[(key[i] >> shift) & mask], 1u);
+            const uint32_t pos = atomicAdd(&sm.cnt[(key[i] - kmin) >> shift], 1u);
             sm.buf[pos] = key[i];
         }
     }

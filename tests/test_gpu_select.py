@@ -186,6 +186,57 @@ def test_long_segments_msd_and_skewed_fallback(rt):
             assert_csr_equal(got, want, f"long segments F={F}")
 
 
+@pytest.mark.parametrize("case", ["ragged", "crowded", "over_128k", "two_values", "one_value",
+                                  "both_signs_mid"])
+def test_sort_edge_cases(rt, case):
+    """Per-query sort edges: a segment just above one CTA's 16384 ids
+    (ragged MSD split), a dense id run with far outliers (crowded buckets),
+    a segment over 131072 ids, duplicate ids (two values; one value, all
+    keys equal), and mid-size segments whose ids straddle zero (value-range
+    buckets must not crowd)."""
+    everything = np.array([[-INF, -INF, INF, INF]], np.float32)
+    rng = np.random.default_rng(13)
+    queries = everything
+    if case == "ragged":
+        n = 16391
+        ids = rng.permutation(n).astype(np.int32) * np.int32(3)
+        rects = random_case("uniform", n, 21)
+        queries = np.concatenate([everything, np.array([[0.0, 0.0, 0.999, 0.9995]], np.float32)])
+    elif case == "crowded":
+        n = 60_000
+        ids = np.arange(n, dtype=np.int32)
+        ids[::6000] += np.int32(1 << 20)
+        rects = random_case("uniform", n, 22)
+    elif case == "over_128k":
+        n = 140_000
+        ids = rng.permutation(n).astype(np.int32)
+        rects = random_case("uniform", n, 23)
+        queries = np.concatenate([everything, np.array([[0.0, 0.0, 0.95, 0.98]], np.float32)])
+    elif case == "two_values":
+        n = 30_000
+        ids = np.where(np.arange(n) % 2 == 0, 7, 8).astype(np.int32)
+        rects = random_case("uniform", n, 24)
+    elif case == "one_value":
+        n = 20_000
+        ids = np.full(n, -5, np.int32)
+        rects = random_case("uniform", n, 25)
+    else:
+        n = 12_000
+        ids = (rng.permutation(n) - n // 2).astype(np.int32)
+        rects = random_case("uniform", n, 26)
+        lo = rng.random((40, 2)).astype(np.float32) * np.float32(0.5)
+        queries = np.concatenate([lo, lo + np.float32(0.45)], axis=1).astype(np.float32)
+    want = oracle.Tree(rects, ids, 16).select(queries)
+    if case == "both_signs_mid":
+        c = np.diff(want[0])
+        assert ((c > 256) & (c <= 16384)).sum() > 20
+    else:
+        assert np.diff(want[0]).max() > 16384
+    for F in (16, 64):
+        got = select_gpu(rt, rects, ids, queries, fanout=F)
+        assert_csr_equal(got, want, f"{case} F={F}")
+
+
 def test_crowded_buckets_fall_back_to_lsd(rt):
     """Dense id runs plus a few far outliers crowd the shared-memory buckets
     of mid-size segments; the LSD fallback must give the same result."""
