@@ -103,6 +103,7 @@ typedef struct rtree_select_opts {
 
 typedef struct rtree rtree_t;               /* opaque; owns device memory */
 typedef struct rtree_result rtree_result_t; /* opaque; owns device memory */
+typedef struct rtree_pending rtree_pending_t; /* opaque; a host-result select in flight */
 
 typedef struct rtree_info {
     int64_t n;            /* indexed rectangles */
@@ -144,6 +145,14 @@ RTREE_API rtree_status rtree_build(const float *rects, const int32_t *ids, int64
 
 /* Releases the tree's device memory.  NULL is ignored. */
 RTREE_API void rtree_free(rtree_t *tree);
+
+/*
+ * Releases the tree's device memory in the order of `stream`: work already
+ * enqueued on that stream may still read the tree, and work on other
+ * streams is not waited for (rtree_free may wait for the whole device).
+ * The handle is invalid on return.  NULL is ignored.
+ */
+RTREE_API void rtree_free_async(rtree_t *tree, void *stream);
 
 /* Fills *info.  Errors: RTREE_EINVAL for NULL arguments. */
 RTREE_API rtree_status rtree_get_info(const rtree_t *tree, rtree_info_t *info);
@@ -365,6 +374,34 @@ RTREE_API rtree_status rtree_range_select_host(const rtree_t *tree, const float 
                                                const rtree_select_opts_t *opts, void *stream,
                                                int64_t *offsets, int32_t *ids, int64_t capacity,
                                                int64_t *total);
+
+/*
+ * rtree_range_select_host_async -- rtree_range_select_host that returns
+ * once all of its work and copies are enqueued, so that the caller can start
+ * the next call (or build the next tree) while this call's results are
+ * still travelling to host memory.  The count pass still runs before the
+ * return: *total is valid on return (and RTREE_EOVERFLOW is reported then,
+ * as by rtree_range_select_host).  On RTREE_OK, *pending is the call in
+ * flight, or NULL if it completed already (an empty result); offsets and ids
+ * are valid only after rtree_pending_wait(*pending) returns RTREE_OK.  The
+ * tree, the queries and `stream` may be reused or freed (rtree_free_async on
+ * `stream`) right away.  Small results the host needs during the call (the
+ * total, chunk bounds, error flags) travel through page-locked mapped
+ * memory written by a kernel, not through a copy, so they never wait behind
+ * the copies of earlier calls.
+ */
+RTREE_API rtree_status rtree_range_select_host_async(const rtree_t *tree, const float *queries, int64_t q,
+                                                     const rtree_select_opts_t *opts, void *stream,
+                                                     int64_t *offsets, int32_t *ids, int64_t capacity,
+                                                     int64_t *total, rtree_pending_t **pending);
+
+/*
+ * Waits until a pending host-result select has written its offsets and ids,
+ * releases it and returns its status (device-side errors of the call, e.g.
+ * RTREE_ETIMEOUT, are reported here).  NULL returns RTREE_OK.  Every pending
+ * call must be waited for exactly once.
+ */
+RTREE_API rtree_status rtree_pending_wait(rtree_pending_t *pending);
 
 RTREE_API rtree_status rtree_join(const rtree_t *r, const rtree_t *s, void *stream, rtree_result_t **out);
 

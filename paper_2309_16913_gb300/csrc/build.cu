@@ -404,21 +404,16 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     if (n == 0)
         return RTREE_OK;
 
-    {  // reject NaN and inverted rectangles
-        DevBuf<unsigned long long> bad(s);
-        RT_TRY(bad.alloc(1, "validation flag"));
-        RT_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
-        {
-            KernelTimer kt_("validate", s);
-            k_validate<<<blocks_for(n), kThreads, 0, s>>>(rects, n, bad.p);
-            RT_LAUNCH();
-        }
-        unsigned long long h = 0;
-        RT_CUDA(cudaMemcpyAsync(&h, bad.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-        RT_CUDA(cudaStreamSynchronize(s));
-        if (h != ~0ull)
-            return fail(RTREE_EINVAL,
-                        "rectangle %llu has a NaN coordinate or xmin > xmax or ymin > ymax", h);
+    // NaN and inverted rectangles are looked for first; the verdict is read
+    // with the root box at the end (the build's control flow does not depend
+    // on the coordinates, and an invalid input only wastes the build).
+    DevBuf<unsigned long long> bad(s);
+    RT_TRY(bad.alloc(1, "validation flag"));
+    RT_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
+    {
+        KernelTimer kt_("validate", s);
+        k_validate<<<blocks_for(n), kThreads, 0, s>>>(rects, n, bad.p);
+        RT_LAUNCH();
     }
 
     // ---- bottom-up packing
@@ -604,9 +599,29 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
                 k_ranges_up<<<blocks_for(P), kThreads, 0, s>>>(meta.p, t->level_base[e], P);
             RT_LAUNCH();
         }
-        RT_CUDA(cudaMemcpyAsync(t->root_mbr, boxes[H - 1]->p, sizeof(float4),
-                                cudaMemcpyDeviceToHost, s));
-        RT_CUDA(cudaStreamSynchronize(s));
+        // the validation verdict and the root box reach the host through a
+        // mailbox (no copy-engine queue to wait behind)
+        MailboxRef mb;
+        RT_TRY(mailbox_get(&mb.m));
+        PostList pl{};
+        pl.src[0] = bad.p;
+        pl.words[0] = 2;
+        pl.at[0] = 0;
+        pl.src[1] = boxes[H - 1]->p;
+        pl.words[1] = 4;
+        pl.at[1] = 2;
+        pl.n = 2;
+        RT_TRY(mailbox_post(mb.m, pl, s));
+        RT_TRY(mailbox_wait(mb.m));
+        const volatile uint32_t *w = mb.m.h;
+        const unsigned long long h = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
+        if (h != ~0ull)
+            return fail(RTREE_EINVAL,
+                        "rectangle %llu has a NaN coordinate or xmin > xmax or ymin > ymax", h);
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t v = w[2 + c];
+            memcpy(&t->root_mbr[c], &v, 4);
+        }
     }
     t->mbr = mbr.release();
     t->meta = meta.release();

@@ -230,6 +230,19 @@ void rtree_free(rtree_t *t)
     delete t;
 }
 
+void rtree_free_async(rtree_t *t, void *stream)
+{
+    if (!t)
+        return;
+    DeviceGuard guard(t->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dfree(t->mbr, s);
+    dfree(t->meta, s);
+    dfree(t->nbox, s);
+    dfree(t->ids, s);
+    delete t;
+}
+
 rtree_status rtree_get_info(const rtree_t *t, rtree_info_t *info)
 {
     clear_error();
@@ -366,42 +379,84 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
     }
 }
 
-rtree_status rtree_range_select_host(const rtree_t *t, const float *queries, int64_t q,
-                                     const rtree_select_opts_t *opts, void *stream, int64_t *offsets,
-                                     int32_t *ids, int64_t capacity, int64_t *total)
+namespace {
+
+rtree_status select_host_call(const char *name, const rtree_t *t, const float *queries, int64_t q,
+                              const rtree_select_opts_t *opts, void *stream, int64_t *offsets,
+                              int32_t *ids, int64_t capacity, int64_t *total, rtree_pending_t **pending)
 {
-    clear_error();
     if (!t || !offsets || !total || capacity < 0 || (capacity > 0 && !ids))
-        return fail(RTREE_EINVAL, "rtree_range_select_host: bad argument");
+        return fail(RTREE_EINVAL, "%s: bad argument", name);
     *total = 0;
     if (q < 0 || q >= (int64_t)INT32_MAX)
-        return fail(RTREE_EINVAL, "rtree_range_select_host: q = %lld out of range", (long long)q);
+        return fail(RTREE_EINVAL, "%s: q = %lld out of range", name, (long long)q);
     if (q > 0 && !queries)
-        return fail(RTREE_EINVAL, "rtree_range_select_host: queries is NULL");
+        return fail(RTREE_EINVAL, "%s: queries is NULL", name);
     const bool sorted = !(opts && opts->unsorted);
     const int mapping = opts ? opts->mapping : RTREE_MAP_AUTO;
     if (mapping < RTREE_MAP_AUTO || mapping > RTREE_MAP_WORK_QUEUE)
-        return fail(RTREE_EINVAL, "rtree_range_select_host: unknown mapping %d", mapping);
+        return fail(RTREE_EINVAL, "%s: unknown mapping %d", name, mapping);
     const int order = opts ? opts->order : RTREE_ORDER_INPUT;
     if (order != RTREE_ORDER_INPUT && order != RTREE_ORDER_HILBERT)
-        return fail(RTREE_EINVAL, "rtree_range_select_host: unknown order %d", order);
+        return fail(RTREE_EINVAL, "%s: unknown order %d", name, order);
     try {
         DeviceGuard guard(t->device);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         DevBuf<float4> qtmp(s);
         const float4 *dq = nullptr;
         RT_TRY(stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq));
-        rtree_status st = range_select_host(t, dq, q, sorted, mapping, order, s, offsets, ids, capacity, total);
-        if (st == RTREE_OK) {
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess)
-                st = fail(RTREE_ECUDA, "rtree_range_select_host: %s", cudaGetErrorString(e));
-        }
-        timing_resolve();
-        return st;
+        return range_select_host_begin(t, dq, q, sorted, mapping, order, s, offsets, ids, capacity, total,
+                                       pending);
     } catch (...) {
-        return fail(RTREE_ENOMEM, "rtree_range_select_host: host allocation failed");
+        return fail(RTREE_ENOMEM, "%s: host allocation failed", name);
     }
+}
+
+}  // namespace
+
+rtree_status rtree_range_select_host(const rtree_t *t, const float *queries, int64_t q,
+                                     const rtree_select_opts_t *opts, void *stream, int64_t *offsets,
+                                     int32_t *ids, int64_t capacity, int64_t *total)
+{
+    clear_error();
+    rtree_pending_t *p = nullptr;
+    rtree_status st = select_host_call("rtree_range_select_host", t, queries, q, opts, stream, offsets, ids,
+                                       capacity, total, &p);
+    if (p) {
+        const rtree_status st2 = range_select_host_finish(p);
+        st = st != RTREE_OK ? st : st2;
+    }
+    if (st == RTREE_OK) {
+        DeviceGuard guard(t->device);
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess)
+            st = fail(RTREE_ECUDA, "rtree_range_select_host: %s", cudaGetErrorString(e));
+    }
+    timing_resolve();
+    return st;
+}
+
+rtree_status rtree_range_select_host_async(const rtree_t *t, const float *queries, int64_t q,
+                                           const rtree_select_opts_t *opts, void *stream, int64_t *offsets,
+                                           int32_t *ids, int64_t capacity, int64_t *total,
+                                           rtree_pending_t **pending)
+{
+    clear_error();
+    if (!pending)
+        return fail(RTREE_EINVAL, "rtree_range_select_host_async: pending is NULL");
+    *pending = nullptr;
+    return select_host_call("rtree_range_select_host_async", t, queries, q, opts, stream, offsets, ids,
+                            capacity, total, pending);
+}
+
+rtree_status rtree_pending_wait(rtree_pending_t *pending)
+{
+    clear_error();
+    if (!pending)
+        return RTREE_OK;
+    const rtree_status st = range_select_host_finish(pending);
+    timing_resolve();
+    return st;
 }
 
 rtree_status rtree_range_select_stats(const rtree_t *t, const float *queries, int64_t q, void *stream,

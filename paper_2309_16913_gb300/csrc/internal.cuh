@@ -339,11 +339,49 @@ rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, 
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int fanout, int layout,
                         bool sort_children, cudaStream_t s, rtree *t);
 
+// ------------------------------------------------------------- mailboxes
+// Page-locked host words mapped into the device, plus an event: a kernel
+// stores small results there and the host reads them once the event has
+// completed, so such reads never queue behind large copies on a copy engine
+// (mailbox.cu).  Mailboxes come from a per-device pool.
+constexpr int kMailboxWords = 256;
+struct Mailbox {
+    uint32_t *h = nullptr;  // host view
+    uint32_t *d = nullptr;  // device view
+    cudaEvent_t ev = nullptr;
+    int device = -1;
+};
+// Up to 8 device sources: words[i] 32-bit words from src[i] go to word at[i].
+struct PostList {
+    const void *src[8];
+    int words[8];
+    int at[8];
+    int n;
+};
+rtree_status mailbox_get(Mailbox *m);
+void mailbox_put(Mailbox *m);
+// Enqueues the copy kernel on s, then records m.ev on s.
+rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s);
+rtree_status mailbox_wait(const Mailbox &m);
+struct MailboxRef {
+    Mailbox m;
+    MailboxRef() = default;
+    MailboxRef(const MailboxRef &) = delete;
+    MailboxRef &operator=(const MailboxRef &) = delete;
+    ~MailboxRef() { mailbox_put(&m); }
+};
+
 // Range select whose result is copied, chunk by chunk, to host memory while
-// later chunks are still being selected (see rtree_range_select_host).
-rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t q, bool sorted,
-                               int mapping, int order, cudaStream_t s, int64_t *h_off, int32_t *h_ids,
-                               int64_t capacity, int64_t *h_total);
+// later chunks are still being selected (see rtree_range_select_host).  On
+// success *pending is the call still in flight (its copies run on a stream
+// of its own), or null when nothing is left to wait for; finish it with
+// range_select_host_finish.
+rtree_status range_select_host_begin(const rtree *t, const float4 *queries, int64_t q, bool sorted,
+                                     int mapping, int order, cudaStream_t s, int64_t *h_off,
+                                     int32_t *h_ids, int64_t capacity, int64_t *h_total,
+                                     rtree_pending **pending);
+// Waits for the copies, checks the device flags, frees everything of p.
+rtree_status range_select_host_finish(rtree_pending *p);
 
 // Range select for device queries (float4 rows); order is RTREE_ORDER_*.
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t q, bool sorted,
@@ -371,3 +409,16 @@ rtree_status tree_join(const rtree *r, const rtree *s_tree, bool prune, cudaStre
                        rtree_result *res);
 
 }  // namespace rt
+
+// A host-result select still in flight (rtree_range_select_host_async): its
+// result copies run on `cs`; `ids` and `off` are the device buffers they
+// read, freed on `cs` when the call is finished.
+struct rtree_pending {
+    int device = 0;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[33] = {};
+    rt::Mailbox flags;  // the device flags, posted behind the last chunk
+    int32_t *ids = nullptr;
+    int64_t *off = nullptr;
+};
+

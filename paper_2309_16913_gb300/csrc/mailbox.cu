@@ -1,0 +1,93 @@
+// mailbox.cu -- small device results delivered to the host without a copy
+// engine.
+//
+// A mailbox is a block of page-locked host memory mapped into the device's
+// address space, plus an event.  A kernel stores the values into it, the
+// event is recorded behind that kernel, and the host waits for the event and
+// reads the words.  A cudaMemcpyAsync of a few bytes would instead wait in a
+// copy engine's queue behind every larger copy already queued there (such as
+// gigabytes of an earlier call's results still going to the host), which
+// would serialize calls that are meant to overlap.  Mailboxes are pooled per
+// device: allocating page-locked memory synchronizes the device, so it only
+// happens the first time a mailbox is needed.
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace rt {
+namespace {
+
+std::mutex g_mu;
+std::vector<Mailbox> g_free[64];
+
+__global__ void k_post(PostList l, uint32_t *__restrict__ dst)
+{
+    const int i = threadIdx.x;
+    if (i >= l.n)
+        return;
+    const uint32_t *src = static_cast<const uint32_t *>(l.src[i]);
+    for (int w = 0; w < l.words[i]; ++w)
+        dst[l.at[i] + w] = src[w];
+}
+
+}  // namespace
+
+rtree_status mailbox_get(Mailbox *m)
+{
+    int dev = 0;
+    RT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64)
+        return fail(RTREE_EINVAL, "device %d out of range", dev);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        if (!g_free[dev].empty()) {
+            *m = g_free[dev].back();
+            g_free[dev].pop_back();
+            return RTREE_OK;
+        }
+    }
+    Mailbox n;
+    n.device = dev;
+    void *h = nullptr;
+    RT_CUDA(cudaHostAlloc(&h, kMailboxWords * sizeof(uint32_t), cudaHostAllocMapped | cudaHostAllocPortable));
+    n.h = static_cast<uint32_t *>(h);
+    void *d = nullptr;
+    cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&n.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaFreeHost(h);
+        return fail(RTREE_ECUDA, "mailbox: %s", cudaGetErrorString(e));
+    }
+    n.d = static_cast<uint32_t *>(d);
+    *m = n;
+    return RTREE_OK;
+}
+
+void mailbox_put(Mailbox *m)
+{
+    if (!m->h)
+        return;
+    std::lock_guard<std::mutex> g(g_mu);
+    g_free[m->device].push_back(*m);
+    *m = Mailbox{};
+}
+
+rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s)
+{
+    if (l.n > 0) {
+        k_post<<<1, 32, 0, s>>>(l, m.d);
+        RT_LAUNCH();
+    }
+    RT_CUDA(cudaEventRecord(m.ev, s));
+    return RTREE_OK;
+}
+
+rtree_status mailbox_wait(const Mailbox &m)
+{
+    RT_CUDA(cudaEventSynchronize(m.ev));
+    return RTREE_OK;
+}
+
+}  // namespace rt

@@ -785,20 +785,70 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     return RTREE_OK;
 }
 
-// Host-result form.  One count pass over the batch fixes every query's
-// offset; the offsets come back to the host first, which both answers the
-// caller and cuts the batch into chunks of about equal id counts.  Each
-// chunk's second pass (descriptors, then the segmented sort; or the scatter
-// pass unsorted) runs on `s`, and when it is done its ids are copied to the
-// caller's buffer on a second stream while the next chunk runs.  Chunks of
-// about 128M ids (at most 32 of them) balance the exposed ends (the first
-// chunk's select, the last chunk's copy) against per-chunk launch costs.
-rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
-                               int mapping, int order, cudaStream_t s, int64_t *h_off, int32_t *h_ids,
-                               int64_t capacity, int64_t *h_total)
+// Results in host memory.  One count pass over the whole batch fixes the
+// offsets; a small device kernel cuts the batch into chunks of about equal
+// id counts and posts the totals and chunk bounds to a mailbox (so the host
+// reads them without waiting behind copies still queued by earlier calls).
+// Each chunk's second pass (descriptors, then the segmented sort; or the
+// scatter pass unsorted) runs on `s`, and when it is done its ids are copied
+// to the caller's buffer on a stream of the call's own while the next chunk
+// runs; the offsets go first on that stream.  Chunks of about 128M ids (at
+// most 32 of them) balance the exposed ends (the first chunk's select, the
+// last chunk's copy) against per-chunk launch costs.  The call returns once
+// everything is enqueued; range_select_host_finish waits for the copies.
+constexpr int kHostMaxChunks = 32;
+constexpr int64_t kHostChunkIds = int64_t(128) << 20;
+
+// Mailbox layout of the count pass's summary (int64 words).
+enum { MB_TOTAL = 0, MB_LEAF, MB_RNG, MB_FLAGS, MB_CHUNKS, MB_BOUND,
+       MB_BOFF = MB_BOUND + kHostMaxChunks + 1, MB_WORDS = MB_BOFF + kHostMaxChunks + 1 };
+static_assert(2 * MB_WORDS <= kMailboxWords, "mailbox too small");
+
+// Thread k finds chunk bound k: the first query whose ids start at or after
+// k * total / chunks (a lower bound over the offsets).
+__global__ void k_chunk_plan(const int64_t *__restrict__ off, const int64_t *__restrict__ off_leaf,
+                             const int64_t *__restrict__ off_rng, const int32_t *__restrict__ flags,
+                             int64_t Q, int64_t *__restrict__ mb)
 {
-    constexpr int kMaxChunks = 32;
-    constexpr int64_t kChunkIds = int64_t(128) << 20;
+    const int64_t total = off[Q];
+    int64_t nc = total / kHostChunkIds + 1;
+    nc = nc < kHostMaxChunks ? nc : kHostMaxChunks;
+    nc = nc < Q ? nc : Q;
+    const int k = threadIdx.x;
+    if (k == 0) {
+        mb[MB_TOTAL] = total;
+        mb[MB_LEAF] = off_leaf ? off_leaf[Q] : 0;
+        mb[MB_RNG] = off_rng ? off_rng[Q] : 0;
+        mb[MB_FLAGS] = flags[0];
+        mb[MB_CHUNKS] = nc;
+    }
+    if (k <= nc) {
+        int64_t b = Q;
+        if (k == 0) {
+            b = 0;
+        } else if (k < nc) {
+            const int64_t want = total / nc * k;
+            int64_t lo = 0, hi = Q;
+            while (lo < hi) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (off[mid] < want)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            b = lo;
+        }
+        mb[MB_BOUND + k] = b;
+        mb[MB_BOFF + k] = off[b];
+    }
+}
+
+rtree_status range_select_host_begin(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
+                                     int mapping, int order, cudaStream_t s, int64_t *h_off,
+                                     int32_t *h_ids, int64_t capacity, int64_t *h_total,
+                                     rtree_pending **pending)
+{
+    *pending = nullptr;
     *h_total = 0;
     if (Q == 0 || t->nodes == 0) {
         memset(h_off, 0, (size_t)(Q + 1) * sizeof(int64_t));
@@ -814,9 +864,9 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
     RT_TRY(cnt.alloc(Q, "select counts"));
     RT_TRY(off.alloc(Q + 1, "select offsets"));
     RT_TRY(flags.alloc(2, "select flags"));
-    RT_TRY(ctr.alloc(1 + kMaxChunks, "select work counters"));
+    RT_TRY(ctr.alloc(1 + kHostMaxChunks, "select work counters"));
     RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
-    RT_CUDA(cudaMemsetAsync(ctr.p, 0, (1 + kMaxChunks) * sizeof(unsigned long long), s));
+    RT_CUDA(cudaMemsetAsync(ctr.p, 0, (1 + kHostMaxChunks) * sizeof(unsigned long long), s));
     if (order == RTREE_ORDER_HILBERT) {
         RT_TRY(perm.alloc(Q, "query order"));
         RT_TRY(hilbert_order(t, queries, Q, perm.p, s));
@@ -847,84 +897,76 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
         RT_TRY(scan_exclusive(cnt_leaf.p, off_leaf.p, Q, s));
         RT_TRY(scan_exclusive(cnt_rng.p, off_rng.p, Q, s));
     }
-    int64_t h[2] = {0, 0};
-    int32_t hflags = 0;
-    RT_CUDA(cudaMemcpyAsync(h_off, off.p, (Q + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (sorted) {
-        RT_CUDA(cudaMemcpyAsync(&h[0], off_leaf.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        RT_CUDA(cudaMemcpyAsync(&h[1], off_rng.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    }
-    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
+    MailboxRef plan;
+    RT_TRY(mailbox_get(&plan.m));
+    int64_t *mbd = reinterpret_cast<int64_t *>(plan.m.d);
+    k_chunk_plan<<<1, 64, 0, s>>>(off.p, sorted ? off_leaf.p : nullptr, sorted ? off_rng.p : nullptr,
+                                  flags.p, Q, mbd);
+    RT_LAUNCH();
+    RT_CUDA(cudaEventRecord(plan.m.ev, s));
+    RT_TRY(mailbox_wait(plan.m));
+    const volatile int64_t *mb = reinterpret_cast<const volatile int64_t *>(plan.m.h);
+    const int32_t hflags = (int32_t)mb[MB_FLAGS];
     if (hflags & FLAG_TIMEOUT)
         return fail(RTREE_ETIMEOUT, "select count pass: a work-queue wait exceeded its limit");
     if (hflags)
         return fail(RTREE_EINTERNAL, "select count pass reported device flags 0x%x", hflags);
-    const int64_t total = h_off[Q];
+    const int64_t total = mb[MB_TOTAL];
     *h_total = total;
-    if (total > capacity)
-        return fail(RTREE_EOVERFLOW, "rtree_range_select_host: %lld ids, capacity %lld",
-                    (long long)total, (long long)capacity);
-    if (total == 0)
+    if (total > capacity || total == 0) {  // the offsets are the whole answer
+        RT_CUDA(cudaMemcpyAsync(h_off, off.p, (Q + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        RT_CUDA(cudaStreamSynchronize(s));
+        if (total > capacity)
+            return fail(RTREE_EOVERFLOW, "rtree_range_select_host: %lld ids, capacity %lld",
+                        (long long)total, (long long)capacity);
         return RTREE_OK;
+    }
+    const int kChunks = (int)mb[MB_CHUNKS];
+    int64_t bound[kHostMaxChunks + 1], boff[kHostMaxChunks + 1];
+    if (kChunks < 1 || kChunks > kHostMaxChunks)
+        return fail(RTREE_EINTERNAL, "select: bad chunk count %d", kChunks);
+    for (int k = 0; k <= kChunks; ++k) {
+        bound[k] = mb[MB_BOUND + k];
+        boff[k] = mb[MB_BOFF + k];
+    }
+    const int64_t leaf_total = mb[MB_LEAF], rng_total = mb[MB_RNG];
 
     DevBuf<int32_t> ids(s), cursors(s), leaf(s);
     DevBuf<int2> rng(s);
     DevBuf<uint32_t> cperm(s);
     RT_TRY(ids.alloc(total, "select ids"));
     if (sorted) {
-        RT_TRY(leaf.alloc(h[0], "select leaf hits"));
-        RT_TRY(rng.alloc(h[1], "select whole subtrees"));
+        RT_TRY(leaf.alloc(leaf_total, "select leaf hits"));
+        RT_TRY(rng.alloc(rng_total, "select whole subtrees"));
     }
     if (wq) {
         RT_TRY(cursors.alloc(2 * Q, "select cursors"));
         RT_CUDA(cudaMemsetAsync(cursors.p, 0, 2 * Q * sizeof(int32_t), s));
     }
-    // chunk boundaries: query c_k is the first whose ids start at or after k*total/nchunks
-    int64_t nc64 = total / kChunkIds + 1;
-    if (nc64 > kMaxChunks)
-        nc64 = kMaxChunks;
-    if (nc64 > Q)
-        nc64 = Q;
-    const int kChunks = (int)nc64;
-    int64_t bound[kMaxChunks + 1];
-    bound[0] = 0;
-    for (int k = 1; k < kChunks; ++k) {
-        const int64_t want = total / kChunks * k;
-        int64_t lo = bound[k - 1], hi = Q;
-        while (lo < hi) {
-            const int64_t mid = lo + (hi - lo) / 2;
-            if (h_off[mid] < want)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        bound[k] = lo;
-    }
-    bound[kChunks] = Q;
     int64_t max_chunk = 0;
     for (int k = 0; k < kChunks; ++k)
         max_chunk = bound[k + 1] - bound[k] > max_chunk ? bound[k + 1] - bound[k] : max_chunk;
     if (order == RTREE_ORDER_HILBERT)
         RT_TRY(cperm.alloc(max_chunk, "query order"));
 
-    struct CopyStream {
-        cudaStream_t cs = nullptr;
-        cudaEvent_t ev[kMaxChunks] = {};
-        ~CopyStream()
+    struct Pending {  // owns the in-flight state until it is handed out
+        rtree_pending *p = new rtree_pending();
+        ~Pending()
         {
-            if (cs) {
-                cudaStreamSynchronize(cs);
-                cudaStreamDestroy(cs);
-            }
-            for (auto e : ev)
-                if (e)
-                    cudaEventDestroy(e);
+            if (p)
+                range_select_host_finish(p);
         }
-    } cp;
-    RT_CUDA(cudaStreamCreateWithFlags(&cp.cs, cudaStreamNonBlocking));
-    for (int k = 0; k < kChunks; ++k)
-        RT_CUDA(cudaEventCreateWithFlags(&cp.ev[k], cudaEventDisableTiming));
+    } pd;
+    rtree_pending *p = pd.p;
+    p->device = t->device;
+    RT_CUDA(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking));
+    for (int k = 0; k <= kChunks; ++k)
+        RT_CUDA(cudaEventCreateWithFlags(&p->ev[k], cudaEventDisableTiming));
+    RT_TRY(mailbox_get(&p->flags));
+    // the offsets, then each chunk's ids, go to the host on the call's stream
+    RT_CUDA(cudaEventRecord(p->ev[kChunks], s));
+    RT_CUDA(cudaStreamWaitEvent(p->cs, p->ev[kChunks], 0));
+    RT_CUDA(cudaMemcpyAsync(h_off, off.p, (Q + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, p->cs));
     for (int k = 0; k < kChunks; ++k) {
         const int64_t c0 = bound[k], qc = bound[k + 1] - bound[k];
         if (qc == 0)
@@ -962,26 +1004,61 @@ rtree_status range_select_host(const rtree *t, const float4 *queries, int64_t Q,
             src.rng = rng.p;
             src.off_rng = off_rng.p + c0;
             src.tree_ids = t->ids;
-            RT_TRY(segmented_sort_gather(ids.p, off.p + c0, qc, h_off[c0 + qc] - h_off[c0], src, s,
+            RT_TRY(segmented_sort_gather(ids.p, off.p + c0, qc, boff[k + 1] - boff[k], src, s,
                                          flags.p + 1, total));
         }
-        const int64_t a = h_off[c0], b = h_off[c0 + qc];
-        RT_CUDA(cudaEventRecord(cp.ev[k], s));
-        RT_CUDA(cudaStreamWaitEvent(cp.cs, cp.ev[k], 0));
+        const int64_t a = boff[k], b = boff[k + 1];
+        RT_CUDA(cudaEventRecord(p->ev[k], s));
+        RT_CUDA(cudaStreamWaitEvent(p->cs, p->ev[k], 0));
         if (b > a)
             RT_CUDA(cudaMemcpyAsync(h_ids + a, ids.p + a, (b - a) * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                    cp.cs));
+                                    p->cs));
     }
-    int32_t hf2[2] = {0, 0};
-    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
-    RT_CUDA(cudaStreamSynchronize(cp.cs));
-    if (hf2[1])
-        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
-    if (hf2[0] & FLAG_TIMEOUT)
+    PostList fl{};
+    fl.src[0] = flags.p;
+    fl.words[0] = 2;
+    fl.at[0] = 0;
+    fl.n = 1;
+    RT_TRY(mailbox_post(p->flags, fl, s));
+    p->ids = ids.release();
+    p->off = off.release();
+    pd.p = nullptr;
+    *pending = p;
+    return RTREE_OK;
+}
+
+rtree_status range_select_host_finish(rtree_pending *p)
+{
+    DeviceGuard guard(p->device);
+    cudaError_t e = cudaSuccess;
+    if (p->cs)
+        e = cudaStreamSynchronize(p->cs);
+    int32_t hf[2] = {0, 0};
+    if (p->flags.h) {
+        const cudaError_t e2 = cudaEventSynchronize(p->flags.ev);
+        e = e != cudaSuccess ? e : e2;
+        const volatile int32_t *f = reinterpret_cast<const volatile int32_t *>(p->flags.h);
+        hf[0] = f[0];
+        hf[1] = f[1];
+    }
+    if (p->cs) {
+        dfree(p->ids, p->cs);
+        dfree(p->off, p->cs);
+        cudaStreamDestroy(p->cs);
+    }
+    for (auto ev : p->ev)
+        if (ev)
+            cudaEventDestroy(ev);
+    mailbox_put(&p->flags);
+    delete p;
+    if (e != cudaSuccess)
+        return fail(RTREE_ECUDA, "host-result select: %s", cudaGetErrorString(e));
+    if (hf[1])
+        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf[1]);
+    if (hf[0] & FLAG_TIMEOUT)
         return fail(RTREE_ETIMEOUT, "select second pass: a work-queue wait exceeded its limit");
-    if (hf2[0])
-        return fail(RTREE_EINTERNAL, "select second pass reported device flags 0x%x", hf2[0]);
+    if (hf[0])
+        return fail(RTREE_EINTERNAL, "select second pass reported device flags 0x%x", hf[0]);
     return RTREE_OK;
 }
 

@@ -100,6 +100,7 @@ def _bind(lib):
     sigs = {
         "rtree_build": (C.c_int, [vp, vp, i64, C.POINTER(rtree_config_t), vp, C.POINTER(vp)]),
         "rtree_free": (None, [vp]),
+        "rtree_free_async": (None, [vp, vp]),
         "rtree_get_info": (C.c_int, [vp, C.POINTER(rtree_info_t)]),
         "rtree_export": (C.c_int, [vp, vp, vp, vp, vp, vp]),
         "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
@@ -108,6 +109,9 @@ def _bind(lib):
         "rtree_save": (C.c_int, [vp, C.c_char_p, vp]),
         "rtree_range_select_host": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64,
                                               C.POINTER(C.c_int64)]),
+        "rtree_range_select_host_async": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64,
+                                                    C.POINTER(C.c_int64), C.POINTER(vp)]),
+        "rtree_pending_wait": (C.c_int, [vp]),
         "rtree_load": (C.c_int, [C.c_char_p, C.c_int, vp, C.POINTER(vp)]),
         "rtree_range_select_stats": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
         "rtree_range_select_noalloc": (C.c_int, [vp, vp, i64, vp, vp, i64, C.POINTER(C.c_int64), vp]),
@@ -253,9 +257,14 @@ def rtree_load(path: str, device: int = -1, stream=None) -> int:
     return out.value
 
 
-def rtree_free(handle: int) -> None:
+def rtree_free(handle: int, stream=None) -> None:
+    """Frees a tree.  With ``stream`` the release is ordered on that stream
+    (rtree_free_async) and does not wait for work on other streams."""
     if handle:
-        load_library().rtree_free(handle)
+        if stream is None:
+            load_library().rtree_free(handle)
+        else:
+            load_library().rtree_free_async(handle, _stream(stream))
 
 
 def rtree_get_info(handle: int) -> dict:
@@ -297,13 +306,7 @@ def rtree_range_select(handle: int, queries, unsorted: bool = False, mapping: st
     return out.value
 
 
-def rtree_range_select_host(handle: int, queries, offsets, ids, unsorted: bool = False,
-                            mapping: str | int = "auto", order: str | int = "input", stream=None) -> int:
-    """Select into host arrays (NumPy or CPU tensors; pinned memory overlaps
-    the copies with the work).  ``offsets`` int64[q+1], ``ids`` int32
-    [capacity].  Returns the total; raises RTreeError (RTREE_EOVERFLOW) when
-    ids is too small, after offsets have been written."""
-    lib = load_library()
+def _host_select_args(queries, offsets, ids, unsorted, mapping, order):
     qp, q, keep = _as_rows(queries, "queries")
     opts = rtree_select_opts_t()
     opts.unsorted = 1 if unsorted else 0
@@ -319,12 +322,66 @@ def rtree_range_select_host(handle: int, queries, offsets, ids, unsorted: bool =
     op, on = host_ptr(offsets, np.int64, "offsets")
     ip, cap = host_ptr(ids, np.int32, "ids")
     assert on >= q + 1, "offsets needs q+1 entries"
+    return qp, q, keep, opts, op, ip, cap
+
+
+def rtree_range_select_host(handle: int, queries, offsets, ids, unsorted: bool = False,
+                            mapping: str | int = "auto", order: str | int = "input", stream=None) -> int:
+    """Select into host arrays (NumPy or CPU tensors; pinned memory overlaps
+    the copies with the work).  ``offsets`` int64[q+1], ``ids`` int32
+    [capacity].  Returns the total; raises RTreeError (RTREE_EOVERFLOW) when
+    ids is too small, after offsets have been written."""
+    lib = load_library()
+    qp, q, keep, opts, op, ip, cap = _host_select_args(queries, offsets, ids, unsorted, mapping, order)
     total = C.c_int64()
     rc = lib.rtree_range_select_host(handle, qp, q, C.byref(opts), _stream(stream), op, ip if cap else None,
                                      cap, C.byref(total))
     del keep
     _check(rc, lib)
     return total.value
+
+
+class PendingSelect:
+    """A host-result select in flight (rtree_range_select_host_async).
+    ``total`` is known at once; ``wait()`` returns it once the offsets and
+    ids are in host memory.  Every pending select must be waited for."""
+
+    def __init__(self, handle, total, keep):
+        self._h = handle
+        self.total = total
+        self._keep = keep  # inputs the enqueued copies may still read
+
+    def wait(self) -> int:
+        if self._h is not None:
+            lib = load_library()
+            h, self._h = self._h, None
+            rc = lib.rtree_pending_wait(h)
+            self._keep = None
+            _check(rc, lib)
+        return self.total
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            try:
+                self.wait()
+            except Exception:
+                pass
+
+
+def rtree_range_select_host_async(handle: int, queries, offsets, ids, unsorted: bool = False,
+                                  mapping: str | int = "auto", order: str | int = "input",
+                                  stream=None) -> PendingSelect:
+    """rtree_range_select_host that returns once its work and copies are
+    enqueued; the result is in ``offsets``/``ids`` after ``wait()``.  The
+    next call (or tree build) may be started meanwhile."""
+    lib = load_library()
+    qp, q, keep, opts, op, ip, cap = _host_select_args(queries, offsets, ids, unsorted, mapping, order)
+    total = C.c_int64()
+    pend = C.c_void_p()
+    rc = lib.rtree_range_select_host_async(handle, qp, q, C.byref(opts), _stream(stream), op,
+                                           ip if cap else None, cap, C.byref(total), C.byref(pend))
+    _check(rc, lib)
+    return PendingSelect(pend.value, total.value, (keep, queries, offsets, ids))
 
 
 def rtree_range_select_noalloc(handle: int, queries, offsets, ids, stream=None) -> int:

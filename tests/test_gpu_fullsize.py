@@ -86,3 +86,47 @@ def test_join_2m_x_2m_full(rt):
         _, got = res.to_numpy()
         res.close()
     assert np.array_equal(got, want) and len(want) > 10**5
+
+
+def test_scaled_10m_host_results_pipelined(rt):
+    """The end-to-end form: host inputs, results to pinned host memory in
+    about a dozen chunks, two selects in flight at once (as the benchmark's
+    end-to-end loop runs them).  Checked on a seeded oracle sample and for
+    CSR validity over every query."""
+    import torch
+    w = dg.workload("scaled")
+    Q = w.queries.shape[0]
+    t_orc = oracle.Tree(w.rects, w.ids, 64)
+    rng = np.random.default_rng(164)
+    sample = np.sort(rng.choice(Q, 1200, replace=False))
+    o_off, o_ids = t_orc.select(w.queries[sample])
+    stream = torch.cuda.current_stream()
+    h_rects = torch.from_numpy(w.rects).pin_memory()
+    h_ids = torch.from_numpy(w.ids).pin_memory()
+    h_q = torch.from_numpy(w.queries).pin_memory()
+    half = Q // 2
+    off_a = torch.zeros(Q + 1, dtype=torch.int64).pin_memory()
+    off_b = torch.zeros(half + 1, dtype=torch.int64).pin_memory()
+    h = rt.rtree_build(h_rects, h_ids, 64, "aos", stream)
+    with pytest.raises(rt.RTreeError) as e:  # no room: the count pass alone sizes the buffers
+        rt.rtree_range_select_host_async(h, h_q, off_a, torch.empty(0, dtype=torch.int32), stream=stream)
+    assert e.value.status == rt.RTREE_EOVERFLOW
+    need = int(off_a[-1])
+    assert need > 10**9
+    ids_a = torch.empty(need, dtype=torch.int32).pin_memory()
+    ids_b = torch.empty(need, dtype=torch.int32).pin_memory()
+    pa = rt.rtree_range_select_host_async(h, h_q, off_a, ids_a, order="hilbert", stream=stream)
+    pb = rt.rtree_range_select_host_async(h, h_q[:half], off_b, ids_b, order="hilbert", stream=stream)
+    rt.rtree_free(h, stream=stream)
+    total_a, total_b = pa.wait(), pb.wait()
+    off, ids = off_a.numpy(), ids_a.numpy()
+    assert total_a == need and off[-1] == total_a and np.all(np.diff(off) >= 0)
+    assert np.array_equal(off_b.numpy(), off[:half + 1]) and total_b == off[half]
+    assert np.array_equal(ids_b.numpy()[:total_b], ids[:total_b])
+    for k, qi in enumerate(sample):
+        assert np.array_equal(ids[off[qi]:off[qi + 1]], o_ids[o_off[k]:o_off[k + 1]]), f"query {qi}"
+    d = np.diff(ids.astype(np.int64))
+    inner = np.ones(d.size, bool)
+    b = off[1:-1]
+    inner[b[(b > 0) & (b < total_a)] - 1] = False
+    assert np.all(d[inner] > 0), "segment not strictly ascending"

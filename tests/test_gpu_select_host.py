@@ -90,3 +90,67 @@ def test_host_select_overflow_reports_total(rt):
         assert e.value.status == rt.RTREE_EOVERFLOW and str(need) in str(e.value)
         assert np.array_equal(off, want[0])      # offsets are written
         assert np.all(ids == -7)                 # ids untouched
+
+
+def test_async_selects_in_flight_together(rt):
+    """Two host-result selects in flight at once (the second enqueued before
+    the first is waited for, the tree freed stream-ordered in between), waited
+    for in reverse order: both match the oracle."""
+    import torch
+    w = dg.workload("scaled", n=300_000, q=20_000)
+    qa, qb = w.queries[:12_000], w.queries[12_000:]
+    orc = oracle.Tree(w.rects, w.ids, 64)
+    want_a, want_b = orc.select(qa), orc.select(qb)
+    stream = torch.cuda.current_stream()
+    bufs = []
+    for want, n in ((want_a, qa.shape[0]), (want_b, qb.shape[0])):
+        bufs.append((torch.zeros(n + 1, dtype=torch.int64).pin_memory(),
+                     torch.full((int(want[0][-1]) + 3,), -7, dtype=torch.int32).pin_memory()))
+    h = rt.rtree_build(w.rects, w.ids, 64, "aos", stream)
+    pa = rt.rtree_range_select_host_async(h, qa, bufs[0][0], bufs[0][1], order="hilbert", stream=stream)
+    pb = rt.rtree_range_select_host_async(h, qb, bufs[1][0], bufs[1][1], stream=stream)
+    rt.rtree_free(h, stream=stream)
+    assert pa.total == want_a[0][-1] and pb.total == want_b[0][-1]
+    assert pb.wait() == want_b[0][-1]
+    assert pa.wait() == want_a[0][-1]
+    for (off, ids), want, name in ((bufs[0], want_a, "a"), (bufs[1], want_b, "b")):
+        total = int(want[0][-1])
+        assert_csr_equal((off.numpy(), ids.numpy()[:total]), want, name)
+        assert np.all(ids.numpy()[total:] == -7)
+
+
+def test_async_overflow_and_empty(rt):
+    w = dg.workload("plain", n=20_000, q=500)
+    want = oracle.brute_select(w.rects, w.queries, w.ids)
+    need = int(want[0][-1])
+    with rt.RTree(w.rects, w.ids, fanout=16) as t:
+        off = np.zeros(501, np.int64)
+        ids = np.full(need - 1, -7, np.int32)
+        with pytest.raises(rt.RTreeError) as e:
+            rt.rtree_range_select_host_async(t.handle, w.queries, off, ids)
+        assert e.value.status == rt.RTREE_EOVERFLOW
+        assert np.array_equal(off, want[0]) and np.all(ids == -7)
+        far = np.array([[5, 5, 6, 6], [7, 7, 8, 8]], np.float32)   # nothing there
+        off2 = np.full(3, -1, np.int64)
+        p = rt.rtree_range_select_host_async(t.handle, far, off2, np.zeros(0, np.int32))
+        assert p.total == 0 and p.wait() == 0 and off2.tolist() == [0, 0, 0]
+        p = rt.rtree_range_select_host_async(t.handle, np.zeros((0, 4), np.float32), off2[:1],
+                                             np.zeros(0, np.int32))
+        assert p.wait() == 0 and off2[0] == 0
+
+
+def test_build_reports_invalid_rectangles(rt):
+    """The build's validation verdict (read with the root box at the end of
+    the build) still rejects NaN and inverted rows, and reports the root."""
+    rects = random_case("uniform", 3000, 4)
+    with rt.RTree(rects, None, fanout=16) as t:
+        root = t.info()["root_mbr"]
+        assert np.array_equal(root, np.array([rects[:, 0].min(), rects[:, 1].min(),
+                                              rects[:, 2].max(), rects[:, 3].max()], np.float32))
+    for bad_row in (np.float32([np.nan, 0, 1, 1]), np.float32([0.5, 0, 0.4, 1]),
+                    np.float32([0, 0.5, 1, 0.4])):
+        r = rects.copy()
+        r[1234] = bad_row
+        with pytest.raises(rt.RTreeError) as e:
+            rt.RTree(r, None, fanout=16)
+        assert e.value.status == rt.RTREE_EINVAL and "1234" in str(e.value)
