@@ -170,7 +170,7 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"],
+KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"], "select_bound": ["select.cu", "internal.cuh"],
                   "select_desc": ["select.cu", "internal.cuh"],
                   "select_scatter": ["select.cu", "internal.cuh"],
                   "sort_warp": ["segsort.cu"], "sort_cta": ["segsort.cu"], "sort_gather": ["segsort.cu"],
@@ -202,6 +202,8 @@ def algorithmic_bytes(stats, F, Q, seg_sizes):
     metadata.  Whole subtree: 16 B metadata read + 8 B (lo, hi) written.  Leaf
     hit: 4 B id read + 4 B written.  Sorting an id: 4 B gathered + 4 B written
     (the long-segment path adds three reads and one write for the MSD split).
+    The bound pass visits the internal nodes only; the descriptor pass after
+    it also writes two exact counts per query.
     """
     node = F * 16 + 16
     nodes = stats["nodes_visited"]
@@ -209,12 +211,14 @@ def algorithmic_bytes(stats, F, Q, seg_sizes):
     hits = stats["ids"]
     leaf_hits = hits - stats["ids_from_whole"]
     traverse = nodes * node + whole * 16
+    internal = (nodes - stats["leaves_visited"]) * node + whole * 16
     seg = np.asarray(seg_sizes, dtype=np.int64)
     in_range = lambda lo, hi: int(seg[(seg >= lo) & (seg <= hi)].sum())
     warp_ids, cta_ids, large_ids = in_range(2, 256), in_range(257, 16384), in_range(16385, 1 << 62)
     return {
         "select_count": float(traverse + Q * (16 + 3 * 4)),
-        "select_desc": float(traverse + Q * (16 + 32) + leaf_hits * 8 + whole * 8),
+        "select_bound": float(internal + Q * (16 + 3 * 4)),
+        "select_desc": float(traverse + Q * (16 + 32 + 8) + leaf_hits * 8 + whole * 8),
         "select_scatter": float(traverse + Q * (16 + 16) + hits * 8),
         "sort_warp": float(warp_ids * 8),
         "sort_cta": float(cta_ids * 8),
@@ -337,7 +341,7 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
     # the node-test kernels (count and descriptor passes) against the same peak
-    nt = [k for k in ("select_count", "select_desc") if k in kern and k in algo]
+    nt = [k for k in ("select_bound", "select_count", "select_desc") if k in kern and k in algo]
     roofline_node_test = None
     if nt:
         nt_ms = sum(kern[k][1] for k in nt) / args.steps
@@ -349,7 +353,8 @@ def run_ours(args):
             "algorithmic_bytes_per_step": nt_bytes,
             "traffic": None if any(t is None for t in nt_traffic) else sum(nt_traffic),
             "note": "node bytes include upper tree levels served from L2, so frac can exceed 1; "
-                    "ncu: count pass 95% L2 hit and 80% issue-active (bound by the node tests themselves)"}
+                    "ncu: bound and count passes ~95% L2 hit and ~80% issue-active (bound by the node tests "
+                    "themselves)"}
 
     # ---- end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -511,7 +516,7 @@ def compare_orders(rt, torch, tree, queries, stream, mapping, reps=3):
         trav = sum(v[1] for n, v in k.items() if n.startswith("select_")) / reps
         out[order] = {"ms_per_select": round(e0.elapsed_time(e1) / reps, 3),
                       "traversal_ms": round(trav, 3)}
-    out["what"] = "1M-query select on the built tree, no build; traversal = select_count + select_desc"
+    out["what"] = "1M-query select on the built tree, no build; traversal = select_bound + select_desc"
     return out
 
 
@@ -546,7 +551,7 @@ def run_persist(rt, torch, rects, ids, queries, F, layout, rank):
 
 
 def compare_layouts(rt, torch, rects, ids, queries, stream, F, mapping, order, reps=3):
-    """Traversal kernel time (count + descriptor passes) of the same select
+    """Traversal kernel time (bound + descriptor passes) of the same select
     on trees built in each node layout: D0 (aos), D1 (soa), D2 (lohi)."""
     out = {}
     for layout in ("aos", "soa", "lohi"):
@@ -562,7 +567,7 @@ def compare_layouts(rt, torch, rects, ids, queries, stream, F, mapping, order, r
             rt.rtree_timing_enable(False)
             k = rt.rtree_timing_get()
         out[layout] = {n: round(v[1] / reps, 3) for n, v in k.items()
-                       if n in ("select_count", "select_desc")}
+                       if n in ("select_bound", "select_count", "select_desc")}
     out["what"] = f"F={F}, {mapping}, {order} order: traversal kernel ms per 1M-query select"
     return out
 

@@ -311,7 +311,8 @@ rtree_status select_enqueue(const rtree *t, const float4 *queries, int64_t q, in
 // rng[off_rng[i] .. off_rng[i+1]).  rng may be null (no ranges).
 struct SortSources {
     const int32_t *leaf;
-    const int64_t *off_leaf;
+    const int64_t *off_leaf;  // segment i's leaf hits start at off_leaf[i] and end at
+    const int32_t *leaf_len;  // off_leaf[i] + leaf_len[i] if leaf_len is set, else off_leaf[i+1]
     const int2 *rng;
     const int64_t *off_rng;
     const int32_t *tree_ids;

@@ -66,6 +66,12 @@ __device__ __forceinline__ int class_of(int64_t n)
     return C_LARGE;
 }
 
+// End of segment i's leaf hits in S.leaf.
+__device__ __forceinline__ int64_t leaf_end(const SortSources &S, int64_t i)
+{
+    return S.leaf_len ? S.off_leaf[i] + S.leaf_len[i] : S.off_leaf[i + 1];
+}
+
 // Segments of length 1 are written directly (class -1 otherwise).
 __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_t *__restrict__ lists,
                            int64_t stride, int64_t *__restrict__ large_tmp,
@@ -82,13 +88,13 @@ __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_
         // a segment whose output or sources reach past a buffer's capacity is
         // skipped (the caller sees the totals exceed the capacities)
         if (len > 0 && (off[i + 1] > out_cap ||
-                        (S.leaf_cap && S.off_leaf[i + 1] > S.leaf_cap) ||
+                        (S.leaf_cap && leaf_end(S, i) > S.leaf_cap) ||
                         (S.rng && S.rng_cap && S.off_rng[i + 1] > S.rng_cap)))
             len = 0;
         const int cls = class_of(len);
         if (len == 1) {  // a single id: copy it from its source
             int32_t v;
-            if (S.off_leaf[i + 1] > S.off_leaf[i])
+            if (leaf_end(S, i) > S.off_leaf[i])
                 v = S.leaf[S.off_leaf[i]];
             else
                 v = S.tree_ids[S.rng[S.off_rng[i]].x];
@@ -118,7 +124,7 @@ __global__ void k_classify(const int64_t *__restrict__ off, int64_t nseg, int32_
 __device__ __forceinline__ void warp_gather(int32_t *__restrict__ sm, const SortSources &S,
                                             int64_t i, int lane)
 {
-    const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+    const int64_t l0 = S.off_leaf[i], l1 = leaf_end(S, i);
     for (int64_t e = l0 + lane; e < l1; e += 32)
         sm[e - l0] = S.leaf[e];
     int pos = (int)(l1 - l0);
@@ -286,7 +292,7 @@ __device__ __forceinline__ void cta_gather(CtaSmem<THREADS> &sm, const SortSourc
 {
     constexpr int W = THREADS / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+    const int64_t l0 = S.off_leaf[i], l1 = leaf_end(S, i);
     int64_t r0 = 0, r1 = 0;
     if (S.rng) {
         r0 = S.off_rng[i];
@@ -728,7 +734,7 @@ __global__ void __launch_bounds__(1024)
         int32_t *dst = out + off[i];
         if (tmp_off[b] + (off[i + 1] - off[i]) > scratch_cap)
             continue;  // over the scratch capacity: reported by k_msd_partition
-        const int64_t l0 = S.off_leaf[i], l1 = S.off_leaf[i + 1];
+        const int64_t l0 = S.off_leaf[i], l1 = leaf_end(S, i);
         if (S.leaf + l0 != dst)
             for (int64_t e = l0 + threadIdx.x; e < l1; e += 1024)
                 dst[e - l0] = S.leaf[e];

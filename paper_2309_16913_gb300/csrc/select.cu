@@ -42,7 +42,11 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-enum { PASS_COUNT = 0, PASS_SCATTER = 1, PASS_DESC = 2 };
+// PASS_BOUND is the count pass stopped above the leaves: an intersecting leaf
+// child that is not inside the query is not visited but reserves F slots (an
+// upper bound on its hits); whole subtrees are counted exactly.  It sizes a
+// descriptor pass whose leaf-hit slots are such bounds.
+enum { PASS_COUNT = 0, PASS_SCATTER = 1, PASS_DESC = 2, PASS_BOUND = 3 };
 enum { FLAG_STACK = 1, FLAG_COUNT_MISMATCH = 2, FLAG_TIMEOUT = 4 };
 
 // Copies ids[lo, hi) to out[0, hi-lo) with the whole warp.
@@ -150,8 +154,16 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         const int j = sub + c * G;
         const bool hit = node >= 0 && j < m.y && meets(b[c], q);
         const bool cont = hit && !leaf && inside(b[c], q);
-        const bool push = hit && !leaf && !cont;
+        // bound pass: children of this node are leaves (all children of a
+        // node are on one level), so they are reserved, not visited
+        const bool slot = PASS == PASS_BOUND && hit && !leaf && !cont && m.x >= t.leaf_base;
+        const bool push = hit && !leaf && !cont && !slot;
         const bool emit = hit && leaf;
+        if (PASS == PASS_BOUND) {
+            const int r = F * __popc(__ballot_sync(RT_FULL, slot));
+            wk.lcur += r;
+            wk.cur += r;
+        }
         const unsigned mp = __ballot_sync(RT_FULL, push);
         if (push) {
             const int pos = top + __popc(mp & lt);
@@ -292,7 +304,7 @@ __global__ void __launch_bounds__(kThreads)
         if (lane == 0) {
             if (wk.overflow)
                 atomicOr(flags, FLAG_STACK);
-            if (PASS == PASS_COUNT) {
+            if (PASS == PASS_COUNT || PASS == PASS_BOUND) {
                 io.counts[qi] = (int32_t)wk.cur;
                 if (io.counts_leaf)
                     io.counts_leaf[qi] = (int32_t)wk.lcur;
@@ -301,6 +313,11 @@ __global__ void __launch_bounds__(kThreads)
             } else if (PASS == PASS_SCATTER) {
                 if (wk.cur != sg.lim - sg.base)
                     atomicOr(flags, FLAG_COUNT_MISMATCH);
+            } else if (io.counts) {  // leaf slots are bounds: report the exact counts
+                if (wk.lcur > sg.llim - sg.lbase || wk.rcur != sg.rlim - sg.rbase)
+                    atomicOr(flags, FLAG_COUNT_MISMATCH);
+                io.counts[qi] = (int32_t)wk.cur;
+                io.counts_leaf[qi] = (int32_t)wk.lcur;
             } else {
                 if (wk.lcur != sg.llim - sg.lbase || wk.rcur != sg.rlim - sg.rbase)
                     atomicOr(flags, FLAG_COUNT_MISMATCH);
@@ -502,6 +519,7 @@ SelectKernel pick_pass(int pass)
 {
     return pass == PASS_COUNT     ? k_select<F, LAYOUT, PASS_COUNT>
            : pass == PASS_SCATTER ? k_select<F, LAYOUT, PASS_SCATTER>
+           : pass == PASS_BOUND   ? k_select<F, LAYOUT, PASS_BOUND>
                                   : k_select<F, LAYOUT, PASS_DESC>;
 }
 
@@ -528,7 +546,10 @@ SelectKernel pick(int F, int layout, int pass)
 
 const char *pass_name(int pass)
 {
-    return pass == PASS_COUNT ? "select_count" : pass == PASS_SCATTER ? "select_scatter" : "select_desc";
+    return pass == PASS_COUNT     ? "select_count"
+           : pass == PASS_SCATTER ? "select_scatter"
+           : pass == PASS_BOUND   ? "select_bound"
+                                  : "select_desc";
 }
 
 rtree_status launch(int pass, const rtree *t, const float4 *q, int64_t Q, const SelIO &io,
@@ -656,6 +677,89 @@ rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree
     return RTREE_OK;
 }
 
+// Sorted select, warp per query.  The bound pass stops above the leaves and
+// gives each query F leaf-hit slots per intersecting leaf (whole subtrees
+// exactly); the descriptor pass fills the slots and reports every query's
+// exact counts, whose scan gives the final offsets; the sort reads each
+// query's leaf hits from the start of its slots.  Against an exact count
+// pass this skips the leaf level once (three quarters of the node visits).
+rtree_status range_select_bounded(const rtree *t, const float4 *queries, int64_t Q, int order,
+                                  cudaStream_t s, rtree_result *res, DevBuf<int64_t> &off)
+{
+    DevBuf<int32_t> cnt(s), cnt_leaf(s), cnt_rng(s), flags(s);
+    DevBuf<unsigned long long> ctr(s);
+    DevBuf<int64_t> off_leaf(s), off_rng(s);
+    DevBuf<uint32_t> perm(s);
+    RT_TRY(cnt.alloc(Q, "select counts"));
+    RT_TRY(cnt_leaf.alloc(Q, "select counts"));
+    RT_TRY(cnt_rng.alloc(Q, "select counts"));
+    RT_TRY(flags.alloc(2, "select flags"));  // [0] select passes, [1] sort
+    RT_TRY(ctr.alloc(2, "select work counters"));
+    RT_TRY(off_leaf.alloc(Q + 1, "select offsets"));
+    RT_TRY(off_rng.alloc(Q + 1, "select offsets"));
+    RT_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int32_t), s));
+    RT_CUDA(cudaMemsetAsync(ctr.p, 0, 2 * sizeof(unsigned long long), s));
+    if (order == RTREE_ORDER_HILBERT) {
+        RT_TRY(perm.alloc(Q, "query order"));
+        RT_TRY(hilbert_order(t, queries, Q, perm.p, s));
+    }
+    SelIO io = unlimited();
+    io.counts = cnt.p;
+    io.counts_leaf = cnt_leaf.p;
+    io.counts_rng = cnt_rng.p;
+    io.order = perm.p;
+    RT_TRY(launch(PASS_BOUND, t, queries, Q, io, ctr.p, flags.p, s));
+    RT_TRY(scan_exclusive(cnt_leaf.p, off_leaf.p, Q, s));
+    RT_TRY(scan_exclusive(cnt_rng.p, off_rng.p, Q, s));
+    int64_t h[2] = {0, 0};
+    int32_t hflags = 0;
+    RT_CUDA(cudaMemcpyAsync(&h[0], off_leaf.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaMemcpyAsync(&h[1], off_rng.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (hflags)
+        return fail(RTREE_EINTERNAL, "select bound pass reported device flags 0x%x", hflags);
+
+    DevBuf<int32_t> leaf(s);
+    DevBuf<int2> rng(s);
+    RT_TRY(leaf.alloc(h[0], "select leaf hits"));
+    RT_TRY(rng.alloc(h[1], "select whole subtrees"));
+    SelIO so = unlimited();
+    so.off_leaf = off_leaf.p;
+    so.off_rng = off_rng.p;
+    so.leaf_out = leaf.p;
+    so.rng_out = rng.p;
+    so.order = perm.p;
+    so.counts = cnt.p;            // exact ids per query
+    so.counts_leaf = cnt_leaf.p;  // exact leaf hits (the bounds are scanned already)
+    RT_TRY(launch(PASS_DESC, t, queries, Q, so, ctr.p + 1, flags.p, s));
+    RT_TRY(scan_exclusive(cnt.p, off.p, Q, s));
+    int64_t total = 0;
+    RT_CUDA(cudaMemcpyAsync(&total, off.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    DevBuf<int32_t> ids(s);
+    RT_TRY(ids.alloc(total, "select ids"));
+    SortSources src{};
+    src.leaf = leaf.p;
+    src.off_leaf = off_leaf.p;
+    src.leaf_len = cnt_leaf.p;
+    src.rng = rng.p;
+    src.off_rng = off_rng.p;
+    src.tree_ids = t->ids;
+    RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s, flags.p + 1));
+    int32_t hf2[2] = {0, 0};
+    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    if (hf2[1])
+        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
+    if (hf2[0])
+        return fail(RTREE_EINTERNAL, "select descriptor pass reported device flags 0x%x", hf2[0]);
+    res->total = total;
+    res->offsets = off.release();
+    res->ids = ids.release();
+    return RTREE_OK;
+}
+
 }  // namespace
 
 rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool sorted,
@@ -670,6 +774,8 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         return empty_result(Q, off, s, res);
     if (!pick(t->fanout, t->layout, PASS_COUNT))
         return fail(RTREE_EINVAL, "unsupported fanout %d", t->fanout);
+    if (sorted && !wq)
+        return range_select_bounded(t, queries, Q, order, s, res, off);
 
     DevBuf<int32_t> cnt(s), cnt_leaf(s), cnt_rng(s), flags(s);
     DevBuf<unsigned long long> ctr(s);
