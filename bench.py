@@ -341,7 +341,7 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
     # the node-test kernels (count and descriptor passes) against the same peak
-    nt = [k for k in ("select_bound", "select_count", "select_desc") if k in kern and k in algo]
+    nt = [k for k in ("select_bound", "select_count", "select_desc") if k in kern and kern[k][0] > 0 and k in algo]
     roofline_node_test = None
     if nt:
         nt_ms = sum(kern[k][1] for k in nt) / args.steps
