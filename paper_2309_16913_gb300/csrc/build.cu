@@ -404,7 +404,7 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     if (n == 0)
         return RTREE_OK;
 
-    // NaN and inverted rectangles are looked for first; the verdict is read
+    // NaN and inverted rectangles are looked for first; the outcome is read
     // with the root box at the end (the build's control flow does not depend
     // on the coordinates, and an invalid input only wastes the build).
     DevBuf<unsigned long long> bad(s);
@@ -599,7 +599,7 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
                 k_ranges_up<<<blocks_for(P), kThreads, 0, s>>>(meta.p, t->level_base[e], P);
             RT_LAUNCH();
         }
-        // the validation verdict and the root box reach the host through a
+        // the validation outcome and the root box reach the host through a
         // mailbox (no copy-engine queue to wait behind)
         MailboxRef mb;
         RT_TRY(mailbox_get(&mb.m));

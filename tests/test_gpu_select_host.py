@@ -140,7 +140,7 @@ def test_async_overflow_and_empty(rt):
 
 
 def test_build_reports_invalid_rectangles(rt):
-    """The build's validation verdict (read with the root box at the end of
+    """The build's validation outcome (read with the root box at the end of
     the build) still rejects NaN and inverted rows, and reports the root."""
     rects = random_case("uniform", 3000, 4)
     with rt.RTree(rects, None, fanout=16) as t:
