@@ -359,6 +359,9 @@ struct PostList {
     int at[8];
     int n;
 };
+// Enqueues the copy kernel only: words go to dst, a device view of mapped
+// host memory (usable inside a graph capture).
+rtree_status post_words(const PostList &l, uint32_t *dst, cudaStream_t s);
 rtree_status mailbox_get(Mailbox *m);
 void mailbox_put(Mailbox *m);
 // Enqueues the copy kernel on s, then records m.ev on s.

@@ -74,12 +74,19 @@ void mailbox_put(Mailbox *m)
     *m = Mailbox{};
 }
 
-rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s)
+rtree_status post_words(const PostList &l, uint32_t *dst, cudaStream_t s)
 {
     if (l.n > 0) {
-        k_post<<<1, 32, 0, s>>>(l, m.d);
+        KernelTimer kt_("mailbox_post", s);
+        k_post<<<1, 32, 0, s>>>(l, dst);
         RT_LAUNCH();
     }
+    return RTREE_OK;
+}
+
+rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s)
+{
+    RT_TRY(post_words(l, m.d, s));
     RT_CUDA(cudaEventRecord(m.ev, s));
     return RTREE_OK;
 }

@@ -43,7 +43,8 @@ struct rtree_plan {
     float4 *queries = nullptr;
     rt::SelectBuffers b{};
     void *block = nullptr;            // one device allocation holding the buffers
-    int64_t *host = nullptr;          // pinned: totals [3] + flags (2 x int32)
+    int64_t *host = nullptr;          // mapped page-locked: totals [3] + flags (2 x int32)
+    int64_t *host_dev = nullptr;      // its device view, written by the graph's last kernel
     cudaStream_t cap_stream = nullptr;
     std::vector<rt::Graph> graphs;
     int64_t last_q = 0;
@@ -118,8 +119,9 @@ rtree_status allocate(rtree_plan *p)
     }
     b.leaf_cap = b.rng_cap = b.ids_cap = C;
     b.wq_cap = wq_cap;
-    RT_CUDA(cudaMallocHost(reinterpret_cast<void **>(&p->host), 64));
+    RT_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&p->host), 64, cudaHostAllocMapped | cudaHostAllocPortable));
     memset(p->host, 0, 64);
+    RT_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&p->host_dev), p->host, 0));
     return RTREE_OK;
 }
 
@@ -131,13 +133,17 @@ rtree_status capture(rtree_plan *p, int64_t qb, Graph *out)
     timing_capture_begin();
     rtree_status st = select_enqueue(p->tree, p->queries, qb, p->mapping, p->b, s);
     if (st == RTREE_OK) {
-        cudaError_t e1 = cudaMemcpyAsync(p->host, p->b.off + qb, 8, cudaMemcpyDeviceToHost, s);
-        cudaError_t e2 = cudaMemcpyAsync(p->host + 1, p->b.off_leaf + qb, 8, cudaMemcpyDeviceToHost, s);
-        cudaError_t e3 = cudaMemcpyAsync(p->host + 2, p->b.off_rng + qb, 8, cudaMemcpyDeviceToHost, s);
-        cudaError_t e4 = cudaMemcpyAsync(p->host + 3, p->b.flags, 8, cudaMemcpyDeviceToHost, s);
-        cudaError_t e = e1 ? e1 : e2 ? e2 : e3 ? e3 : e4;
-        if (e != cudaSuccess)
-            st = fail(RTREE_ECUDA, "rtree_plan_run: capture of the result copy: %s", cudaGetErrorString(e));
+        // the totals and flags are stored into mapped host memory by a kernel:
+        // a small copy would wait behind other plans' result copies
+        PostList pl{};
+        const void *src[4] = {p->b.off + qb, p->b.off_leaf + qb, p->b.off_rng + qb, p->b.flags};
+        for (int i = 0; i < 4; ++i) {
+            pl.src[i] = src[i];
+            pl.words[i] = 2;
+            pl.at[i] = 2 * i;
+        }
+        pl.n = 4;
+        st = post_words(pl, reinterpret_cast<uint32_t *>(p->host_dev), s);
     }
     const long long launches = timing_capture_end();
     cudaGraph_t graph = nullptr;
