@@ -13,7 +13,9 @@
 //                 thread sorts whole buckets in registers with a bitonic
 //                 network; a crowded bucket sends the segment to a stable
 //                 LSD radix sort (8-bit digits);
-//   > 16384       gathered into place, partitioned by its top differing bits
+//   16385..40960  the same with one CTA of 1024 threads, 40 keys each (160 KB
+//                 of shared memory; a crowded one goes on to the next path);
+//   > 40960       gathered into place, partitioned by its top differing bits
 //                 into buckets of about 8K ids (MSD step through a scratch
 //                 area), each bucket then sorted like a mid-size segment.
 // LSD passes whose digit is equal for all keys are skipped (from the AND and
@@ -30,7 +32,9 @@ namespace {
 
 constexpr int kBins = 256;
 constexpr int kItems = 16;              // keys per thread in the CTA sort
-constexpr int kCtaMax = 1024 * kItems;  // 16384: largest in-shared-memory segment
+constexpr int kCtaMax = 1024 * kItems;  // 16384: largest segment of the 16-key CTA sorts
+constexpr int kItemsBig = 40;           // keys per thread of the CTA sort above kCtaMax
+constexpr int kCtaBigMax = 1024 * kItemsBig;
 constexpr uint32_t kSign = 0x80000000u;
 constexpr int kBucketBitsMax = 12;      // at most 4096 buckets
 constexpr int kBucketDensity = 1;       // 2^(ceil(log2 n) - 1) buckets of the key range
@@ -40,6 +44,7 @@ constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to 
 enum {
     C_W1 = 0, C_W2, C_W4, C_W8,       // warp sorts, 32*K ids
     C_T128, C_T256, C_T512, C_T1024,  // CTA sorts, 16 ids per thread
+    C_T1024B,                         // CTA sort, kItemsBig ids per thread
     C_LARGE,                          // MSD partition first
     C_COUNT
 };
@@ -63,6 +68,7 @@ __device__ __forceinline__ int class_of(int64_t n)
     if (n <= 4096) return C_T256;
     if (n <= 8192) return C_T512;
     if (n <= kCtaMax) return C_T1024;
+    if (n <= kCtaBigMax) return C_T1024B;
     return C_LARGE;
 }
 
@@ -233,10 +239,10 @@ __global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ l
 }
 
 // ------------------------------------------------------------ CTA sort
-template <int THREADS>
+template <int THREADS, int ITEMS = kItems>
 struct CtaSmem {
     static constexpr int W = THREADS / 32;
-    uint32_t buf[THREADS * kItems];
+    uint32_t buf[THREADS * ITEMS];
     union {
         uint32_t cnt[1 << kBucketBitsMax];  // bucket sort: per-bucket counts, then ends
         struct {                            // LSD ranks
@@ -257,8 +263,8 @@ struct CtaSmem {
 
 // Exclusive block scan of one int per thread (uses sm.wsum); returns the
 // prefix and writes the block total to *total.
-template <int THREADS>
-__device__ __forceinline__ int block_scan_int(CtaSmem<THREADS> &sm, int v, int *total)
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ int block_scan_int(CtaSmem<THREADS, ITEMS> &sm, int v, int *total)
 {
     constexpr int W = THREADS / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -287,8 +293,8 @@ __device__ __forceinline__ int block_scan_int(CtaSmem<THREADS> &sm, int v, int *
 // The CTA copies segment i's ids into sm.buf[0 .. n), flipped to keys.  The
 // first chunk of range descriptors is requested before the leaf hits are
 // copied, so both loads are in flight together.
-template <int THREADS>
-__device__ __forceinline__ void cta_gather(CtaSmem<THREADS> &sm, const SortSources &S, int64_t i)
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ void cta_gather(CtaSmem<THREADS, ITEMS> &sm, const SortSources &S, int64_t i)
 {
     constexpr int W = THREADS / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -332,8 +338,8 @@ __device__ __forceinline__ void cta_gather(CtaSmem<THREADS> &sm, const SortSourc
 }
 
 // The CTA copies keys src[0 .. n) (xor flip) into sm.buf.
-template <int THREADS>
-__device__ __forceinline__ void cta_load(CtaSmem<THREADS> &sm, const uint32_t *__restrict__ src,
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ void cta_load(CtaSmem<THREADS, ITEMS> &sm, const uint32_t *__restrict__ src,
                                          int n, uint32_t flip)
 {
     for (int p = threadIdx.x; p < n; p += THREADS)
@@ -342,8 +348,8 @@ __device__ __forceinline__ void cta_load(CtaSmem<THREADS> &sm, const uint32_t *_
 }
 
 // Block-wide AND and OR of the keys' bits; every thread gets AND ^ OR.
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_and, uint32_t a_or)
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS, ITEMS> &sm, uint32_t a_and, uint32_t a_or)
 {
     constexpr int W = THREADS / 32;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -368,8 +374,8 @@ __device__ __forceinline__ uint32_t block_diff(CtaSmem<THREADS> &sm, uint32_t a_
 }
 
 // Block-wide minimum and maximum of the keys; every thread gets both.
-template <int THREADS>
-__device__ __forceinline__ void block_minmax(CtaSmem<THREADS> &sm, uint32_t &kmin, uint32_t &kmax)
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ void block_minmax(CtaSmem<THREADS, ITEMS> &sm, uint32_t &kmin, uint32_t &kmax)
 {
     constexpr int W = THREADS / 32;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -430,14 +436,14 @@ __device__ __forceinline__ void bucket_network(uint32_t *buf, int s0, int c)
 // signs) from crowding into a few buckets.
 // Returns false, having written the unsorted ids to dst, if a bucket holds
 // more than kBucketCrowded keys (the caller then sorts dst with LSD).
-template <int THREADS>
-__device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *__restrict__ dst,
+template <int THREADS, int ITEMS>
+__device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS, ITEMS> &sm, int32_t *__restrict__ dst,
                                                 int n)
 {
-    uint32_t key[kItems];
+    uint32_t key[ITEMS];
     uint32_t kmin = 0xffffffffu, kmax = 0;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         if (i * THREADS >= n)
             break;
         const int p = i * THREADS + threadIdx.x;
@@ -471,7 +477,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         sm.crowded = 0;
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         if (i * THREADS >= n)
             break;
         if (i * THREADS + threadIdx.x < n)
@@ -502,7 +508,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS> &sm, int32_t *_
         return false;
     }
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         if (i * THREADS >= n)
             break;
         if (i * THREADS + threadIdx.x < n) {
@@ -547,18 +553,35 @@ __device__ __forceinline__ void push_crowded(SegDesc *list, unsigned long long *
         list[slot] = SegDesc{dst, dst, n, 0};
 }
 
+// The MSD path's segment list, its scratch offsets and the header counters.
+struct LongList {
+    int32_t *list;
+    int64_t *tmp;
+    unsigned long long *hdr;
+};
+
+// Lists segment seg (n ids) for the MSD path, with a scratch range of its own.
+__device__ __forceinline__ void push_large(const LongList &lg, int32_t seg, int64_t n)
+{
+    const unsigned long long slot = atomicAdd(lg.hdr + C_LARGE, 1ull);
+    lg.list[slot] = seg;
+    lg.tmp[slot] = (int64_t)atomicAdd(lg.hdr + HDR_SCRATCH, (unsigned long long)n);
+}
+
 // One CTA per listed segment.  BUCKETS: the list holds SegDesc entries whose
 // keys sit in `scratch`; otherwise segment ids whose ids are gathered from S.
-template <int THREADS, bool BUCKETS>
+// ITEMS keys per thread; a segment of more than 16384 ids whose buckets are
+// crowded goes to the MSD path.
+template <int THREADS, bool BUCKETS, int ITEMS = kItems>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_sort_cta(const void *__restrict__ list, const unsigned long long *__restrict__ count,
                int64_t list_cap, const int64_t *__restrict__ off, SortSources S,
                const uint32_t *__restrict__ scratch, int32_t *__restrict__ out,
                SegDesc *__restrict__ crowded, unsigned long long *__restrict__ n_crowded,
-               int64_t crowded_cap)
+               int64_t crowded_cap, LongList lg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    CtaSmem<THREADS> &sm = *reinterpret_cast<CtaSmem<THREADS> *>(smem_raw);
+    CtaSmem<THREADS, ITEMS> &sm = *reinterpret_cast<CtaSmem<THREADS, ITEMS> *>(smem_raw);
     const int64_t cnt = list_len(count, list_cap);
     for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
         int64_t dof;
@@ -567,19 +590,23 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
             const SegDesc d = static_cast<const SegDesc *>(list)[b];
             dof = d.dst;
             n = d.n;
-            if (n > THREADS * kItems)
+            if (n > THREADS * ITEMS)
                 continue;
             cta_load<THREADS>(sm, scratch + d.src, n, 0u);
         } else {
             const int32_t seg = static_cast<const int32_t *>(list)[b];
             dof = off[seg];
             n = (int)(off[seg + 1] - dof);
-            if (n > THREADS * kItems)
+            if (n > THREADS * ITEMS)
                 continue;
             cta_gather<THREADS>(sm, S, seg);
         }
-        if (!cta_bucket_sort<THREADS>(sm, out + dof, n) && threadIdx.x == 0)
-            push_crowded(crowded, n_crowded, crowded_cap, dof, n);
+        if (!cta_bucket_sort<THREADS>(sm, out + dof, n) && threadIdx.x == 0) {
+            if (ITEMS > kItems)  // longer than the LSD fallback takes: the MSD path re-gathers it
+                push_large(lg, static_cast<const int32_t *>(list)[b], n);
+            else
+                push_crowded(crowded, n_crowded, crowded_cap, dof, n);
+        }
     }
 }
 
@@ -779,10 +806,10 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// One CTA per segment longer than kCtaMax: partitions its keys by their top
-// b differing bits (2^b buckets of about kCtaMax/2) into the scratch area and
-// lists every bucket for the CTA sort (or, if a bucket is still too long,
-// for the global LSD fallback).
+// One CTA per listed long segment (over 40960 ids, or over 16384 with crowded
+// buckets): partitions its keys by their top b differing bits (2^b buckets
+// of about kCtaMax/2) into the scratch area and lists every bucket for the
+// CTA sort (or, if a bucket is still too long, for the global LSD fallback).
 __global__ void __launch_bounds__(1024)
     k_msd_partition(const int32_t *__restrict__ list, const int64_t *__restrict__ tmp_off,
                     const unsigned long long *__restrict__ count, int64_t list_cap,
@@ -999,15 +1026,16 @@ struct Crowded {
     int64_t cap;
 };
 
-template <int THREADS, bool BUCKETS>
+template <int THREADS, bool BUCKETS, int ITEMS = kItems>
 rtree_status launch_cta(const void *list, const unsigned long long *count, int64_t list_cap,
                         const int64_t *off, const SortSources &S, const uint32_t *scratch,
-                        int32_t *out, const Crowded &cr, cudaStream_t s, const char *name)
+                        int32_t *out, const Crowded &cr, cudaStream_t s, const char *name,
+                        const LongList &lg = LongList{})
 {
     if (list_cap <= 0)
         return RTREE_OK;
-    auto kern = k_sort_cta<THREADS, BUCKETS>;
-    const size_t bytes = sizeof(CtaSmem<THREADS>);
+    auto kern = k_sort_cta<THREADS, BUCKETS, ITEMS>;
+    const size_t bytes = sizeof(CtaSmem<THREADS, ITEMS>);
     RT_TRY(set_smem(kern, bytes));
     int per_sm = 0;
     RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, bytes));
@@ -1016,7 +1044,7 @@ rtree_status launch_cta(const void *list, const unsigned long long *count, int64
         grid = list_cap;
     KernelTimer kt_(name, s);
     kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, count, list_cap, off, S, scratch, out, cr.list,
-                                                cr.count, cr.cap);
+                                                cr.count, cr.cap, lg);
     RT_LAUNCH();
     return RTREE_OK;
 }
@@ -1103,6 +1131,9 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
     RT_TRY(launch_lsd(cr1, out, s));
     if (total <= kCtaMax)
         return RTREE_OK;  // no segment can be long
+    const LongList lg{L(C_LARGE), large_tmp.p, hdr.p};
+    RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_T1024B), H(C_T1024B), cap_of(kCtaMax + 1), offsets, S,
+                                               nullptr, out, cr1, s, "sort_cta", lg)));
 
     // Long segments: gather into place, MSD-partition into the scratch area,
     // then sort the buckets back into place.

@@ -186,11 +186,11 @@ def test_long_segments_msd_and_skewed_fallback(rt):
             assert_csr_equal(got, want, f"long segments F={F}")
 
 
-@pytest.mark.parametrize("case", ["ragged", "crowded", "over_128k", "two_values", "one_value",
-                                  "both_signs_mid"])
+@pytest.mark.parametrize("case", ["ragged", "crowded", "crowded_20k", "over_128k", "two_values",
+                                  "one_value", "both_signs_mid"])
 def test_sort_edge_cases(rt, case):
-    """Per-query sort edges: a segment just above one CTA's 16384 ids
-    (ragged MSD split), a dense id run with far outliers (crowded buckets),
+    """Per-query sort edges: a segment just above 16384 ids (ragged), a
+    dense id run with far outliers (crowded buckets, at 60k and at 20k ids),
     a segment over 131072 ids, duplicate ids (two values; one value, all
     keys equal), and mid-size segments whose ids straddle zero (value-range
     buckets must not crowd)."""
@@ -207,6 +207,11 @@ def test_sort_edge_cases(rt, case):
         ids = np.arange(n, dtype=np.int32)
         ids[::6000] += np.int32(1 << 20)
         rects = random_case("uniform", n, 22)
+    elif case == "crowded_20k":  # crowded in the one-CTA sort above 16384 ids: MSD path
+        n = 20_000
+        ids = np.arange(n, dtype=np.int32)
+        ids[::5000] += np.int32(1 << 20)
+        rects = random_case("uniform", n, 27)
     elif case == "over_128k":
         n = 140_000
         ids = rng.permutation(n).astype(np.int32)
