@@ -7,7 +7,8 @@
 //   2..256 ids    one warp: gather into shared memory, then a bitonic network
 //                 on 1-8 keys per lane in registers (shuffles across lanes,
 //                 swaps inside a lane);
-//   257..16384    one CTA of 128-1024 threads, entirely in shared memory:
+//   257..16384    one CTA of 64-512 threads (32 keys each), entirely in
+//                 shared memory:
 //                 bucket the keys by value within their range (1-4 keys per
 //                 bucket for spread-out ids) with shared atomics, then each
 //                 thread sorts whole buckets in registers with a bitonic
@@ -31,8 +32,9 @@ namespace rt {
 namespace {
 
 constexpr int kBins = 256;
-constexpr int kItems = 16;              // keys per thread in the CTA sort
-constexpr int kCtaMax = 1024 * kItems;  // 16384: largest segment of the 16-key CTA sorts
+constexpr int kItems = 16;              // keys per thread of the LSD fallback (1024 threads)
+constexpr int kCtaMax = 1024 * kItems;  // 16384: longest segment the LSD fallback takes
+constexpr int kItemsMid = 32;           // keys per thread of the CTA sorts up to kCtaMax
 constexpr int kItemsBig = 40;           // keys per thread of the CTA sort above kCtaMax
 constexpr int kCtaBigMax = 1024 * kItemsBig;
 constexpr uint32_t kSign = 0x80000000u;
@@ -43,8 +45,8 @@ constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to 
 // Segment classes (index into the class lists).
 enum {
     C_W1 = 0, C_W2, C_W4, C_W8,       // warp sorts, 32*K ids
-    C_T128, C_T256, C_T512, C_T1024,  // CTA sorts, 16 ids per thread
-    C_T1024B,                         // CTA sort, kItemsBig ids per thread
+    C_CTA2K, C_CTA4K, C_CTA8K, C_CTA16K,  // CTA sorts of 64..512 threads, kItemsMid ids each
+    C_CTA40K,                             // CTA sort of 1024 threads, kItemsBig ids each
     C_LARGE,                          // MSD partition first
     C_COUNT
 };
@@ -64,11 +66,11 @@ __device__ __forceinline__ int class_of(int64_t n)
     if (n <= 64) return C_W2;
     if (n <= 128) return C_W4;
     if (n <= 256) return C_W8;
-    if (n <= 2048) return C_T128;
-    if (n <= 4096) return C_T256;
-    if (n <= 8192) return C_T512;
-    if (n <= kCtaMax) return C_T1024;
-    if (n <= kCtaBigMax) return C_T1024B;
+    if (n <= 2048) return C_CTA2K;
+    if (n <= 4096) return C_CTA4K;
+    if (n <= 8192) return C_CTA8K;
+    if (n <= kCtaMax) return C_CTA16K;
+    if (n <= kCtaBigMax) return C_CTA40K;
     return C_LARGE;
 }
 
@@ -239,12 +241,17 @@ __global__ void __launch_bounds__(256) k_sort_warp(const int32_t *__restrict__ l
 }
 
 // ------------------------------------------------------------ CTA sort
+constexpr int log2_floor(int v) { return v > 1 ? 1 + log2_floor(v / 2) : 0; }
+
 template <int THREADS, int ITEMS = kItems>
 struct CtaSmem {
     static constexpr int W = THREADS / 32;
+    // at most 2^(ceil(log2 n) - 1) <= n/2 buckets are used (and at most 2^12)
+    static constexpr int kCntBits = log2_floor(THREADS * ITEMS / 2) < kBucketBitsMax
+                                        ? log2_floor(THREADS * ITEMS / 2) : kBucketBitsMax;
     uint32_t buf[THREADS * ITEMS];
     union {
-        uint32_t cnt[1 << kBucketBitsMax];  // bucket sort: per-bucket counts, then ends
+        uint32_t cnt[1 << kCntBits];  // bucket sort: per-bucket counts, then ends
         struct {                            // LSD ranks
             uint32_t wcnt[W][kBins];
             uint32_t dcount[kBins];
@@ -466,7 +473,8 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS, ITEMS> &sm, int
     const uint32_t span = kmax - kmin;
     const int width = 32 - __clz(span);
     int bits = (32 - __clz((unsigned)(n - 1))) - kBucketDensity;
-    bits = bits < 1 ? 1 : (bits > kBucketBitsMax ? kBucketBitsMax : bits);
+    constexpr int kMaxBits = CtaSmem<THREADS, ITEMS>::kCntBits;
+    bits = bits < 1 ? 1 : (bits > kMaxBits ? kMaxBits : bits);
     if (bits > width)
         bits = width;
     const int shift = width - bits;
@@ -602,7 +610,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
             cta_gather<THREADS>(sm, S, seg);
         }
         if (!cta_bucket_sort<THREADS>(sm, out + dof, n) && threadIdx.x == 0) {
-            if (ITEMS > kItems)  // longer than the LSD fallback takes: the MSD path re-gathers it
+            if (!BUCKETS && n > kCtaMax)  // longer than the LSD fallback takes: MSD path
                 push_large(lg, static_cast<const int32_t *>(list)[b], n);
             else
                 push_crowded(crowded, n_crowded, crowded_cap, dof, n);
@@ -1124,15 +1132,16 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
     RT_TRY(crowded.alloc(cta_cap > 0 ? cta_cap : 1, "sort crowded list"));
     unsigned long long *n_crowded = hdr.p + HDR_WORDS;  // two counters after the header
     const Crowded cr1{crowded.p, n_crowded, cta_cap};
-    RT_TRY((launch_cta<128, false>(L(C_T128), H(C_T128), cap_of(257), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<256, false>(L(C_T256), H(C_T256), cap_of(2049), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<512, false>(L(C_T512), H(C_T512), cap_of(4097), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<1024, false>(L(C_T1024), H(C_T1024), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    constexpr int M = kItemsMid;
+    RT_TRY((launch_cta<64, false, M>(L(C_CTA2K), H(C_CTA2K), cap_of(257), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<128, false, M>(L(C_CTA4K), H(C_CTA4K), cap_of(2049), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<256, false, M>(L(C_CTA8K), H(C_CTA8K), cap_of(4097), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<512, false, M>(L(C_CTA16K), H(C_CTA16K), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
     RT_TRY(launch_lsd(cr1, out, s));
     if (total <= kCtaMax)
         return RTREE_OK;  // no segment can be long
     const LongList lg{L(C_LARGE), large_tmp.p, hdr.p};
-    RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_T1024B), H(C_T1024B), cap_of(kCtaMax + 1), offsets, S,
+    RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_CTA40K), H(C_CTA40K), cap_of(kCtaMax + 1), offsets, S,
                                                nullptr, out, cr1, s, "sort_cta", lg)));
 
     // Long segments: gather into place, MSD-partition into the scratch area,
@@ -1159,7 +1168,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
         RT_LAUNCH();
     }
     const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
-    RT_TRY((launch_cta<1024, true>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
+    RT_TRY((launch_cta<512, true, kItemsMid>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
     RT_TRY(launch_lsd(cr2, out, s));
     {
         int64_t g2 = desc_cap < (int64_t)sms * 4 ? desc_cap : (int64_t)sms * 4;
