@@ -346,7 +346,7 @@ def run_ours(args):
         roofline["traffic_note"] = traffic_note
     if dominant.startswith("sort_"):
         roofline["note"] = ("the CTA sort is bound by shared-memory work and per-segment latency, not by HBM: "
-                            "ncu shows 48-59% issue active, 49-71% L1/shared throughput and 6-10% of DRAM peak "
+                            "ncu shows 45-53% issue active, barrier and scoreboard stalls and a few % of DRAM peak "
                             "(profiles/select_sort_kernels_profile_case.md)")
     # the node-test kernels (count and descriptor passes) against the same peak
     nt = [k for k in ("select_bound", "select_count", "select_desc") if k in kern and kern[k][0] > 0 and k in algo]
