@@ -1085,6 +1085,80 @@ rtree_status launch_warp(const int32_t *list, const unsigned long long *count, i
     return RTREE_OK;
 }
 
+// Helper streams of this host thread on the current device, created on first
+// use and kept for the thread's life: the sort's independent class kernels
+// run on them beside the call's stream, so that one kernel's tail (its last
+// CTAs finishing while the rest of the GPU idles) overlaps the next.
+constexpr int kSide = 3;
+struct SideStreams {
+    int device = -1;
+    cudaStream_t st[kSide] = {};
+    cudaEvent_t ev[kSide + 1] = {};
+};
+
+rtree_status side_streams(SideStreams **out)
+{
+    constexpr int kMaxDev = 64;
+    static thread_local SideStreams t_side[kMaxDev];
+    int dev = 0;
+    RT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDev)
+        return fail(RTREE_ECUDA, "device %d out of range", dev);
+    SideStreams &sd = t_side[dev];
+    if (sd.device != dev) {
+        for (int i = 0; i < kSide; ++i)
+            RT_CUDA(cudaStreamCreateWithFlags(&sd.st[i], cudaStreamNonBlocking));
+        for (int i = 0; i <= kSide; ++i)
+            RT_CUDA(cudaEventCreateWithFlags(&sd.ev[i], cudaEventDisableTiming));
+        sd.device = dev;
+    }
+    *out = &sd;
+    return RTREE_OK;
+}
+
+// Work enqueued on the side streams after begin() runs after everything
+// enqueued on the main stream before it; the main stream waits for all of it
+// when the Fork is joined or destroyed (also on an early error return, so
+// that buffers freed in the main stream's order outlive their users).
+// Declare it after every buffer the side work uses.
+struct Fork {
+    SideStreams *sd = nullptr;
+    cudaStream_t s = nullptr;
+    bool open = false;
+    rtree_status begin(cudaStream_t main)
+    {
+        s = main;
+        RT_TRY(side_streams(&sd));
+        RT_CUDA(cudaEventRecord(sd->ev[kSide], s));
+        for (int i = 0; i < kSide; ++i)
+            RT_CUDA(cudaStreamWaitEvent(sd->st[i], sd->ev[kSide], 0));
+        open = true;
+        return RTREE_OK;
+    }
+    cudaStream_t side(int i) const { return sd->st[i]; }
+    // The main stream waits for side stream i's work enqueued so far.
+    rtree_status wait(int i)
+    {
+        RT_CUDA(cudaEventRecord(sd->ev[i], sd->st[i]));
+        RT_CUDA(cudaStreamWaitEvent(s, sd->ev[i], 0));
+        return RTREE_OK;
+    }
+    rtree_status join()
+    {
+        if (!open)
+            return RTREE_OK;
+        open = false;
+        for (int i = 0; i < kSide; ++i)
+            RT_TRY(wait(i));
+        return RTREE_OK;
+    }
+    ~Fork()
+    {
+        if (open && join() != RTREE_OK)
+            cudaGetLastError();
+    }
+};
+
 }  // namespace
 
 rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t nseg, int64_t total,
@@ -1123,61 +1197,77 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
     auto H = [&](int c) { return hdr.p + c; };
     // a class can hold at most total / (its smallest length) segments
     auto cap_of = [&](int64_t min_len) { return total / min_len < nseg ? total / min_len : nseg; };
-    RT_TRY(launch_warp<1>(L(C_W1), H(C_W1), cap_of(2), offsets, S, out, s));
-    RT_TRY(launch_warp<2>(L(C_W2), H(C_W2), cap_of(33), offsets, S, out, s));
-    RT_TRY(launch_warp<4>(L(C_W4), H(C_W4), cap_of(65), offsets, S, out, s));
-    RT_TRY(launch_warp<8>(L(C_W8), H(C_W8), cap_of(129), offsets, S, out, s));
     const int64_t cta_cap = cap_of(257);
     DevBuf<SegDesc> crowded(s);
     RT_TRY(crowded.alloc(cta_cap > 0 ? cta_cap : 1, "sort crowded list"));
     unsigned long long *n_crowded = hdr.p + HDR_WORDS;  // two counters after the header
     const Crowded cr1{crowded.p, n_crowded, cta_cap};
-    constexpr int M = kItemsMid;
-    RT_TRY((launch_cta<64, false, M>(L(C_CTA2K), H(C_CTA2K), cap_of(257), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<128, false, M>(L(C_CTA4K), H(C_CTA4K), cap_of(2049), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<256, false, M>(L(C_CTA8K), H(C_CTA8K), cap_of(4097), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY((launch_cta<512, false, M>(L(C_CTA16K), H(C_CTA16K), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
-    RT_TRY(launch_lsd(cr1, out, s));
-    if (total <= kCtaMax)
-        return RTREE_OK;  // no segment can be long
-    const LongList lg{L(C_LARGE), large_tmp.p, hdr.p};
-    RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_CTA40K), H(C_CTA40K), cap_of(kCtaMax + 1), offsets, S,
-                                               nullptr, out, cr1, s, "sort_cta", lg)));
-
-    // Long segments: gather into place, MSD-partition into the scratch area,
-    // then sort the buckets back into place.
+    const bool long_path = total > kCtaMax;  // else no segment can be long
+    // the long path's buffers (segments over 40960 ids, or crowded over 16384)
     DevBuf<uint32_t> scratch(s);
     DevBuf<SegDesc> buckets(s), oversize(s), crowded2(s);
-    RT_TRY(scratch.alloc(scratch_cap, "sort scratch"));
-    RT_TRY(buckets.alloc(desc_cap, "sort buckets"));
-    RT_TRY(oversize.alloc(desc_cap, "sort buckets"));
-    RT_TRY(crowded2.alloc(desc_cap, "sort crowded list"));
-    const int64_t grid = max_large < (int64_t)sms * 2 ? max_large : (int64_t)sms * 2;
-    {
-        KernelTimer kt_("sort_gather", s);
-        k_gather_large<<<(unsigned)grid, 1024, 0, s>>>(L(C_LARGE), H(C_LARGE), max_large, large_tmp.p,
-                                                       scratch_cap, offsets, S, out);
-        RT_LAUNCH();
+    if (long_path) {
+        RT_TRY(scratch.alloc(scratch_cap, "sort scratch"));
+        RT_TRY(buckets.alloc(desc_cap, "sort buckets"));
+        RT_TRY(oversize.alloc(desc_cap, "sort buckets"));
+        RT_TRY(crowded2.alloc(desc_cap, "sort crowded list"));
     }
-    {
-        KernelTimer kt_("sort_msd", s);
-        k_msd_partition<<<(unsigned)grid, 1024, 0, s>>>(
-            L(C_LARGE), large_tmp.p, H(C_LARGE), max_large, scratch_cap, offsets,
-            reinterpret_cast<const uint32_t *>(out), scratch.p, buckets.p, oversize.p, desc_cap,
-            hdr.p, flags);
-        RT_LAUNCH();
+    // Three side streams and the call's stream run the classes side by side:
+    //   side 2: the 40960-id CTA sort, then the long path (which it feeds);
+    //   side 1: the CTA sorts up to 8192 ids;
+    //   side 0: the warp sorts;
+    //   stream: the CTA sort up to 16384 ids, then (after side 1) the LSD
+    //           fallback for crowded segments of all CTA classes up to 16384.
+    // The largest kernels are enqueued first so that smaller ones fill the
+    // SMs their last CTAs leave idle.
+    Fork fk;
+    RT_TRY(fk.begin(s));
+    constexpr int M = kItemsMid;
+    if (long_path) {
+        const cudaStream_t s2 = fk.side(2);
+        const LongList lg{L(C_LARGE), large_tmp.p, hdr.p};
+        RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_CTA40K), H(C_CTA40K), cap_of(kCtaMax + 1), offsets, S,
+                                                   nullptr, out, cr1, s2, "sort_cta", lg)));
+        // Long segments: gather into place, MSD-partition into the scratch
+        // area, then sort the buckets back into place.
+        const int64_t grid = max_large < (int64_t)sms * 2 ? max_large : (int64_t)sms * 2;
+        {
+            KernelTimer kt_("sort_gather", s2);
+            k_gather_large<<<(unsigned)grid, 1024, 0, s2>>>(L(C_LARGE), H(C_LARGE), max_large, large_tmp.p,
+                                                            scratch_cap, offsets, S, out);
+            RT_LAUNCH();
+        }
+        {
+            KernelTimer kt_("sort_msd", s2);
+            k_msd_partition<<<(unsigned)grid, 1024, 0, s2>>>(
+                L(C_LARGE), large_tmp.p, H(C_LARGE), max_large, scratch_cap, offsets,
+                reinterpret_cast<const uint32_t *>(out), scratch.p, buckets.p, oversize.p, desc_cap,
+                hdr.p, flags);
+            RT_LAUNCH();
+        }
+        const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
+        RT_TRY((launch_cta<512, true, kItemsMid>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s2, "sort_bucket")));
+        RT_TRY(launch_lsd(cr2, out, s2));
+        {
+            int64_t g2 = desc_cap < (int64_t)sms * 4 ? desc_cap : (int64_t)sms * 4;
+            KernelTimer kt_("sort_global", s2);
+            k_sort_global<<<(unsigned)g2, 256, 0, s2>>>(oversize.p, H(HDR_OVERSIZE), desc_cap, scratch.p,
+                                                        out);
+            RT_LAUNCH();
+        }
     }
-    const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
-    RT_TRY((launch_cta<512, true, kItemsMid>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s, "sort_bucket")));
-    RT_TRY(launch_lsd(cr2, out, s));
-    {
-        int64_t g2 = desc_cap < (int64_t)sms * 4 ? desc_cap : (int64_t)sms * 4;
-        KernelTimer kt_("sort_global", s);
-        k_sort_global<<<(unsigned)g2, 256, 0, s>>>(oversize.p, H(HDR_OVERSIZE), desc_cap, scratch.p,
-                                                   out);
-        RT_LAUNCH();
-    }
-    return RTREE_OK;
+    RT_TRY((launch_cta<512, false, M>(L(C_CTA16K), H(C_CTA16K), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    const cudaStream_t s1 = fk.side(1), s0 = fk.side(0);
+    RT_TRY((launch_cta<256, false, M>(L(C_CTA8K), H(C_CTA8K), cap_of(4097), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
+    RT_TRY((launch_cta<128, false, M>(L(C_CTA4K), H(C_CTA4K), cap_of(2049), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
+    RT_TRY((launch_cta<64, false, M>(L(C_CTA2K), H(C_CTA2K), cap_of(257), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
+    RT_TRY(launch_warp<8>(L(C_W8), H(C_W8), cap_of(129), offsets, S, out, s0));
+    RT_TRY(launch_warp<4>(L(C_W4), H(C_W4), cap_of(65), offsets, S, out, s0));
+    RT_TRY(launch_warp<2>(L(C_W2), H(C_W2), cap_of(33), offsets, S, out, s0));
+    RT_TRY(launch_warp<1>(L(C_W1), H(C_W1), cap_of(2), offsets, S, out, s0));
+    RT_TRY(fk.wait(1));
+    RT_TRY(launch_lsd(cr1, out, s));
+    return fk.join();
 }
 
 rtree_status segmented_sort(int32_t *ids, const int64_t *offsets, int64_t nseg, int64_t total,
