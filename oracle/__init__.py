@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rtree_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-CFLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11"]
+CFLAGS = ["-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-pthread"]
 
 _lock = threading.Lock()
 _lib = None
@@ -36,7 +36,7 @@ def build_oracle(src: str = _SRC, out: str = _LIB_PATH, force: bool = False) -> 
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm", "-lpthread"], check=True)
     os.replace(tmp, out)
     return out
 
@@ -67,6 +67,10 @@ def _bind(lib):
     lib.orc_brute_select.argtypes = [f32p, i32p, i64, f32p, i64, i64p, C.POINTER(i32p)]
     lib.orc_join.restype = i64
     lib.orc_join.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(i32p)]
+    lib.orc_select_mt.restype = i64
+    lib.orc_select_mt.argtypes = [C.c_void_p, f32p, i64, i64p, C.POINTER(i32p), C.c_int]
+    lib.orc_join_mt.restype = i64
+    lib.orc_join_mt.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(i32p), C.c_int]
     lib.orc_brute_join.restype = i64
     lib.orc_brute_join.argtypes = [f32p, i32p, i64, f32p, i32p, i64, C.POINTER(i32p)]
     lib.orc_free.restype = None
@@ -154,20 +158,30 @@ class Tree:
     def n_nodes(self) -> int:
         return self._lib.orc_tree_nodes(self._h)
 
-    def select(self, queries):
-        """Returns (offsets int64[Q+1], ids int32[total]) with sorted segments."""
+    def select(self, queries, threads: int = 1):
+        """Returns (offsets int64[Q+1], ids int32[total]) with sorted segments.
+        ``threads`` > 1 runs the same select on that many POSIX threads, each
+        on a contiguous run of the queries (orc_select_mt)."""
         q = _rects(queries)
         off = np.zeros(q.shape[0] + 1, dtype=np.int64)
         ptr = C.POINTER(C.c_int32)()
-        total = self._lib.orc_select(self._h, _f(q), q.shape[0], _l(off), C.byref(ptr))
+        if threads > 1:
+            total = self._lib.orc_select_mt(self._h, _f(q), q.shape[0], _l(off), C.byref(ptr), int(threads))
+        else:
+            total = self._lib.orc_select(self._h, _f(q), q.shape[0], _l(off), C.byref(ptr))
         if total < 0:
             raise MemoryError("oracle select failed")
         return off, _take_i32(self._lib, ptr, total)
 
-    def join(self, other: "Tree") -> np.ndarray:
-        """Returns int32[total, 2] (r_id, s_id) pairs, sorted lexicographically."""
+    def join(self, other: "Tree", threads: int = 1) -> np.ndarray:
+        """Returns int32[total, 2] (r_id, s_id) pairs, sorted lexicographically.
+        ``threads`` > 1 splits the traversal's top-level node pairs over that
+        many POSIX threads (orc_join_mt)."""
         ptr = C.POINTER(C.c_int32)()
-        total = self._lib.orc_join(self._h, other._h, C.byref(ptr))
+        if threads > 1:
+            total = self._lib.orc_join_mt(self._h, other._h, C.byref(ptr), int(threads))
+        else:
+            total = self._lib.orc_join(self._h, other._h, C.byref(ptr))
         if total < 0:
             raise MemoryError("oracle join failed")
         return _take_i32(self._lib, ptr, 2 * total).reshape(-1, 2)

@@ -42,10 +42,16 @@
  * +0.  Query results do not depend on the tree at all; the build is fixed
  * only so that a tree built elsewhere can be compared node by node.
  *
+ * For timing on all host cores, orc_select_mt and orc_join_mt run the same
+ * scalar routines on contiguous chunks of the queries (or of the join's
+ * top-level node pairs) in POSIX threads, each into its own output, and
+ * concatenate the outputs; threads share nothing but the read-only trees.
+ *
  * Compile with -O2 -fno-fast-math -ffp-contract=off: float32 sums and
  * comparisons must follow IEEE 754 exactly.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -552,6 +558,239 @@ int64_t orc_join(const otree *r, const otree *s, int32_t **pairs_out)
     qsort(out.v, (size_t)(out.n / 2), 2 * sizeof(int32_t), cmp_pair);
     *pairs_out = out.v;
     return out.n / 2;
+}
+
+/* ------------------------------------------- all-cores forms (for timing) */
+
+typedef struct {
+    const otree *t;
+    const float *queries;
+    int64_t q0, q1;
+    int64_t *counts; /* counts[i - q0] = hits of query i */
+    ivec out;
+    int rc;
+} sel_job;
+
+static void *sel_worker(void *p)
+{
+    sel_job *j = (sel_job *)p;
+    for (int64_t i = j->q0; i < j->q1; i++) {
+        box q = {j->queries[4 * i], j->queries[4 * i + 1], j->queries[4 * i + 2],
+                 j->queries[4 * i + 3]};
+        int64_t start = j->out.n;
+        if (j->t && j->t->root && select_rec(j->t->root, q, &j->out)) {
+            j->rc = -1;
+            return NULL;
+        }
+        qsort(j->out.v + start, (size_t)(j->out.n - start), sizeof(int32_t), cmp_i32);
+        j->counts[i - j->q0] = j->out.n - start;
+    }
+    return NULL;
+}
+
+/* orc_select on `threads` POSIX threads, each taking a contiguous run of the
+ * queries; same contract and result as orc_select. */
+int64_t orc_select_mt(const otree *t, const float *queries, int64_t Q, int64_t *offsets,
+                      int32_t **ids_out, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    if ((int64_t)threads > Q)
+        threads = Q > 0 ? (int)Q : 1;
+    sel_job *jobs = (sel_job *)calloc((size_t)threads, sizeof(sel_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    char *started = (char *)calloc((size_t)threads, 1);
+    if (!jobs || !tid || !started) {
+        free(jobs);
+        free(tid);
+        free(started);
+        return -1;
+    }
+    offsets[0] = 0;
+    for (int k = 0; k < threads; k++) {
+        jobs[k].t = t;
+        jobs[k].queries = queries;
+        jobs[k].q0 = Q * k / threads;
+        jobs[k].q1 = Q * (k + 1) / threads;
+        jobs[k].counts = offsets + 1 + jobs[k].q0;
+        started[k] = pthread_create(&tid[k], NULL, sel_worker, &jobs[k]) == 0;
+        if (!started[k])
+            sel_worker(&jobs[k]);
+    }
+    int64_t total = 0;
+    int rc = 0;
+    for (int k = 0; k < threads; k++) {
+        if (started[k])
+            pthread_join(tid[k], NULL);
+        rc |= jobs[k].rc;
+        total += jobs[k].out.n;
+    }
+    int32_t *ids = rc ? NULL : (int32_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    int64_t at = 0;
+    for (int k = 0; k < threads; k++) {
+        if (ids && jobs[k].out.n)
+            memcpy(ids + at, jobs[k].out.v, (size_t)jobs[k].out.n * sizeof(int32_t));
+        at += jobs[k].out.n;
+        free(jobs[k].out.v);
+    }
+    free(jobs);
+    free(tid);
+    free(started);
+    if (!ids)
+        return -1;
+    for (int64_t i = 0; i < Q; i++)
+        offsets[i + 1] += offsets[i];
+    *ids_out = ids;
+    return total;
+}
+
+typedef struct {
+    const onode *a, *b;
+    box amb, bmb;
+} jcall;
+
+typedef struct {
+    jcall *v;
+    int64_t n, cap;
+} jvec;
+
+static int jvec_push(jvec *c, jcall x)
+{
+    if (c->n == c->cap) {
+        int64_t nc = c->cap ? c->cap * 2 : 64;
+        jcall *p = (jcall *)realloc(c->v, (size_t)nc * sizeof(jcall));
+        if (!p)
+            return -1;
+        c->v = p;
+        c->cap = nc;
+    }
+    c->v[c->n++] = x;
+    return 0;
+}
+
+/* One step of join_rec on a node pair, with the same branching: leaf pairs
+ * go to out, and every recursive call join_rec would make goes to next. */
+static int join_expand(jcall c, ivec *out, jvec *next)
+{
+    const onode *a = c.a, *b = c.b;
+    if (a->height == b->height) {
+        for (int i = 0; i < a->count; i++)
+            for (int j = 0; j < b->count; j++) {
+                if (!intersects(a->mbr[i], b->mbr[j]))
+                    continue;
+                if (a->height == 0) {
+                    if (emit_pair(out, a->id[i], b->id[j]))
+                        return -1;
+                } else {
+                    jcall d = {a->child[i], b->child[j], a->mbr[i], b->mbr[j]};
+                    if (jvec_push(next, d))
+                        return -1;
+                }
+            }
+    } else if (a->height > b->height) {
+        for (int i = 0; i < a->count; i++)
+            if (intersects(a->mbr[i], c.bmb)) {
+                jcall d = {a->child[i], b, a->mbr[i], c.bmb};
+                if (jvec_push(next, d))
+                    return -1;
+            }
+    } else {
+        for (int j = 0; j < b->count; j++)
+            if (intersects(c.amb, b->mbr[j])) {
+                jcall d = {a, b->child[j], c.amb, b->mbr[j]};
+                if (jvec_push(next, d))
+                    return -1;
+            }
+    }
+    return 0;
+}
+
+typedef struct {
+    const jcall *calls;
+    int64_t c0, c1;
+    ivec out;
+    int rc;
+} join_job;
+
+static void *join_worker(void *p)
+{
+    join_job *j = (join_job *)p;
+    for (int64_t k = j->c0; k < j->c1; k++) {
+        const jcall *c = &j->calls[k];
+        if (join_rec(c->a, c->amb, c->b, c->bmb, &j->out)) {
+            j->rc = -1;
+            return NULL;
+        }
+    }
+    return NULL;
+}
+
+/* orc_join on `threads` POSIX threads: the traversal is expanded level by
+ * level from the roots until there are at least 8 node pairs per thread (or
+ * none left), then each thread runs join_rec on a contiguous run of them.
+ * Same contract and result as orc_join. */
+int64_t orc_join_mt(const otree *r, const otree *s, int32_t **pairs_out, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    ivec out = {0, 0, 0};
+    jvec cur = {0, 0, 0}, next = {0, 0, 0};
+    int rc = 0;
+    if (r && s && r->root && s->root) {
+        jcall root = {r->root, s->root, r->root_mbr, s->root_mbr};
+        rc = jvec_push(&cur, root);
+        while (!rc && cur.n > 0 && cur.n < 8 * (int64_t)threads) {
+            next.n = 0;
+            for (int64_t k = 0; k < cur.n && !rc; k++)
+                rc = join_expand(cur.v[k], &out, &next);
+            jvec t = cur;
+            cur = next;
+            next = t;
+        }
+    }
+    int nt = (int64_t)threads > cur.n ? (int)(cur.n > 0 ? cur.n : 1) : threads;
+    join_job *jobs = (join_job *)calloc((size_t)nt, sizeof(join_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)nt, sizeof(pthread_t));
+    char *started = (char *)calloc((size_t)nt, 1);
+    if (!jobs || !tid || !started)
+        rc = -1;
+    for (int k = 0; !rc && k < nt; k++) {
+        jobs[k].calls = cur.v;
+        jobs[k].c0 = cur.n * k / nt;
+        jobs[k].c1 = cur.n * (k + 1) / nt;
+        started[k] = pthread_create(&tid[k], NULL, join_worker, &jobs[k]) == 0;
+        if (!started[k])
+            join_worker(&jobs[k]);
+    }
+    int64_t total = out.n;
+    for (int k = 0; jobs && tid && started && k < nt; k++) {
+        if (started[k])
+            pthread_join(tid[k], NULL);
+        rc |= jobs[k].rc;
+        total += jobs[k].out.n;
+    }
+    int32_t *v = rc ? NULL : (int32_t *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+    int64_t at = 0;
+    if (v && out.n)
+        memcpy(v, out.v, (size_t)out.n * sizeof(int32_t));
+    at = out.n;
+    for (int k = 0; jobs && k < nt; k++) {
+        if (v && jobs[k].out.n)
+            memcpy(v + at, jobs[k].out.v, (size_t)jobs[k].out.n * sizeof(int32_t));
+        at += jobs[k].out.n;
+        free(jobs[k].out.v);
+    }
+    free(jobs);
+    free(tid);
+    free(started);
+    free(out.v);
+    free(cur.v);
+    free(next.v);
+    if (!v)
+        return -1;
+    qsort(v, (size_t)(total / 2), 2 * sizeof(int32_t), cmp_pair);
+    *pairs_out = v;
+    return total / 2;
 }
 
 /* --------------------------------------------- join with sorted-node pruning */

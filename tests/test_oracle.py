@@ -148,6 +148,26 @@ def check_random_vs_brute(lib, seeds=(0, 1), n=300, q=40):
                 assert np.array_equal(pb, pt), (kind, fr, fs, seed)
 
 
+def check_threaded_vs_brute(lib):
+    """The all-cores forms (orc_select_mt, orc_join_mt) equal brute force,
+    with more threads than queries, uneven chunks and unequal tree heights."""
+    for kind, seed in (("uniform", 40), ("grid", 41), ("clustered", 42)):
+        rects = random_case(kind, 900, seed)
+        ids = np.random.default_rng(seed).permutation(900).astype(np.int32) - np.int32(300)
+        qs = random_case(kind, 37, seed + 1)
+        ob, ib = oracle.brute_select(rects, qs, ids, lib=lib)
+        t = oracle.Tree(rects, ids, 4, lib=lib)
+        for threads in (2, 7, 64):
+            ot, it = t.select(qs, threads=threads)
+            assert np.array_equal(ob, ot) and np.array_equal(ib, it), (kind, threads)
+        s = random_case(kind, 700, seed + 2)
+        sid = np.arange(700, dtype=np.int32) * 2 - 5
+        pb = oracle.brute_join(rects, s, ids, sid, lib=lib)
+        for fr, fs, threads in ((4, 16, 3), (2, 32, 8), (16, 2, 5), (64, 64, 4)):
+            pt = oracle.Tree(rects, ids, fr, lib=lib).join(oracle.Tree(s, sid, fs, lib=lib), threads=threads)
+            assert np.array_equal(pt, pb), (kind, fr, fs, threads)
+
+
 def sorted_export_reference(e):
     """From the export of a tree, the export of the same tree with every
     node's entries stably reordered by ascending lx (written independently of
@@ -243,7 +263,8 @@ def check_o5(lib):
 
 
 PIN_SUITE = (check_predicate, check_select_golden, check_join_golden, check_str_golden,
-             check_random_vs_brute, check_sorted_build, check_pruned_join, check_o5)
+             check_random_vs_brute, check_sorted_build, check_pruned_join, check_o5,
+             check_threaded_vs_brute)
 
 
 # -------------------------------------------------------------- the pins
@@ -272,6 +293,10 @@ def test_sorted_children_entries_ascend():
     e = oracle.Tree(rects, None, 16, sort_children=True).export()
     for g, c in enumerate(e["counts"]):
         assert np.all(np.diff(e["mbrs"][g, :c, 0]) >= 0)
+
+
+def test_threaded_forms_match_brute():
+    check_threaded_vs_brute(oracle.load())
 
 
 def test_pruned_join_matches_brute():
@@ -461,6 +486,12 @@ MUTANTS = [
     ("O5 moves the wrong way", "g[i] = pass ? g[i] + step : g[i] - step;",
      "g[i] = pass ? g[i] - step : g[i] + step;"),
     ("O5 one round short", "int rounds = logp + 1;", "int rounds = logp;"),
+    ("threaded select drops each chunk's last query", "jobs[k].q1 = Q * (k + 1) / threads;",
+     "jobs[k].q1 = Q * (k + 1) / threads - (k + 1 < threads);"),
+    ("threaded join expands the wrong child", "jcall d = {a->child[i], b, a->mbr[i], c.bmb};",
+     "jcall d = {a->child[0], b, a->mbr[0], c.bmb};"),
+    ("threaded join expands one level short", "jcall d = {a, b->child[j], c.amb, b->mbr[j]};",
+     "jcall d = {a, b, c.amb, c.bmb};"),
 ]
 
 
@@ -473,7 +504,7 @@ def test_planted_mistakes_are_caught(tmp_path):
         path = tmp_path / f"m{abs(hash(name))}.c"
         path.write_text(src.replace(old, new, 1))
         so = str(path) + ".so"
-        subprocess.run(["gcc", *oracle.CFLAGS, "-o", so, str(path), "-lm"], check=True)
+        subprocess.run(["gcc", *oracle.CFLAGS, "-o", so, str(path), "-lm", "-lpthread"], check=True)
         lib = oracle.load(so)
         caught = False
         for check in PIN_SUITE:
