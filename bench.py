@@ -10,10 +10,11 @@ layout are picked once before the warm-up by timing one step of each
 candidate.  Under torchrun every rank builds and queries its own instance
 (weak scaling; no collective on the data path).
 
-``--impl reference`` times the CPU oracle (plain scalar C, one thread) on the
-same workload instead: the tree is built once, each step selects a fixed
-sample of queries, and ``value`` extrapolates to the full batch
-(1M / (build + per-query time * 1M)).
+``--impl reference`` times the CPU oracle (plain scalar C, on every host
+core, one POSIX thread per core over query chunks) on the same workload
+instead: the tree is built once at fanout 64 (the paper's default), each
+step selects a fixed subset of 65536 queries, and ``value`` extrapolates to
+the full batch (1M / (build + per-query time * 1M)).
 
 Prints one JSON line on rank 0.
 """
@@ -23,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -37,7 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "range queries/s at 10M rects"
 UNIT = "queries/s"
 WORKLOAD = "scaled"
-CPU_SAMPLE_QUERIES = 2000
+CPU_SAMPLE_QUERIES = 65536   # fixed subset of the batch the oracle is timed on
+REF_FANOUT = 64               # the paper's default fanout (Section 5)
 
 
 def parse_args():
@@ -47,7 +50,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fanout", type=int, default=0, help="0: pick by timing 16/32/64")
-    ap.add_argument("--layout", choices=["soa", "aos", "auto"], default="auto")
+    ap.add_argument("--layout", choices=["soa", "aos", "lohi", "auto"], default="auto")
     ap.add_argument("--mapping", choices=["warp_per_query", "work_queue", "auto"], default="auto")
     ap.add_argument("--rects", "--n", dest="n", type=int, default=None,
                     help="override rectangles (testing only)")
@@ -63,6 +66,8 @@ def parse_args():
     ap.add_argument("--order", choices=["auto", "input", "hilbert"], default="auto",
                     help="traversal order of the query batch (auto: the autotuner picks)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner; needs --fanout, --layout, --mapping and --order set")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-n", type=int, default=50_000_000, help="index size of the serving run")
@@ -175,9 +180,12 @@ def source_sha(files):
 
 KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"], "select_bound": ["select.cu", "internal.cuh"],
                   "select_desc": ["select.cu", "internal.cuh"],
+                  "join_scatter": ["join.cu", "internal.cuh"],
+                  "join_pruned_count": ["join.cu", "internal.cuh"],
+                  "join_pruned_scatter": ["join.cu", "internal.cuh"],
                   "select_scatter": ["select.cu", "internal.cuh"],
                   "sort_warp": ["segsort.cu"], "sort_cta": ["segsort.cu"], "sort_gather": ["segsort.cu"],
-                  "sort_msd": ["segsort.cu"], "sort_bucket": ["segsort.cu"],
+                  "sort_msd": ["segsort.cu"], "sort_bucket": ["segsort.cu"], "sort_all": ["segsort.cu"],
                   "scatter": ["radix_sort.cu"], "join_count": ["join.cu", "internal.cuh"]}
 
 
@@ -229,7 +237,116 @@ def algorithmic_bytes(stats, F, Q, seg_sizes):
         "sort_gather": float(large_ids * 8),
         "sort_msd": float(large_ids * 16),
         "sort_bucket": float(large_ids * 8),
+        # the whole segmented sort as one span (its class kernels run side by side)
+        "sort_all": float((warp_ids + cta_ids + large_ids) * 8 + large_ids * 24),
     }
+
+
+def join_roofline(st, Fr, Fs, kern, hbm, peak_kind, clk):
+    """Roofline of the join's traversal kernels (count and scatter passes of
+    every level, one launch each), from the traversal counters.
+
+    Bytes: a node pair tested at equal heights reads both nodes' entries
+    ((Fr + Fs) * 16 B) and two node records (32 B); a one-sided descent
+    reads the taller node's entries and the other node's box.  The scatter
+    pass also writes 8 B per child pair or result pair it emits.  Tests: a
+    node pair at equal heights takes Fr * Fs predicate tests, a one-sided
+    descent F tests.  The issue-slot side needs instruction counts from ncu
+    (profiles/ncu_metrics.txt) and is reported when they were taken on the
+    current source."""
+    eq = st["pairs_equal_internal"] + st["pairs_leaf"]
+    node_bytes = eq * ((Fr + Fs) * 16 + 32) + st["pairs_r_descends"] * (Fr * 16 + 32) + \
+        st["pairs_s_descends"] * (Fs * 16 + 32)
+    visited = eq + st["pairs_r_descends"] + st["pairs_s_descends"]
+    emitted = (visited - 1) + st["pairs_found"]
+    tests = eq * Fr * Fs + st["pairs_r_descends"] * Fr + st["pairs_s_descends"] * Fs
+    names = sorted(kern)
+    ms = sum(v[1] for v in kern.values())
+    if ms <= 0:
+        return None
+    algo = 2 * node_bytes + 8 * emitted
+    achieved = algo / (ms / 1e3) / 1e9
+    out = {"kernels": names, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+           "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "ms_per_step": round(ms, 4),
+           "algorithmic_bytes_per_step": int(algo), "node_pairs": int(visited),
+           "predicate_tests_per_s": round(2 * tests / (ms / 1e3), 1)}
+    issue = issue_fraction([n for n in names], visited, ms, clk)
+    if issue:
+        out["issue"] = issue
+    return out
+
+
+def node_test_roofline(kern, algo, stats, steps, hbm, peak_kind, clk):
+    """Per node-test kernel: the logical rate (algorithmic bytes, upper tree
+    levels included though L2 serves them), the DRAM rate from ncu's DRAM
+    bytes per node visit on the profile case scaled to this run's visits,
+    and the issue-slot use; `bound` names the larger fraction."""
+    internal = stats["nodes_visited"] - stats["leaves_visited"]
+    units = {"select_bound": internal, "select_desc": stats["nodes_visited"],
+             "select_count": stats["nodes_visited"]}
+    out = {}
+    for k in ("select_bound", "select_count", "select_desc"):
+        if k not in kern or kern[k][0] == 0 or k not in algo:
+            continue
+        ms = kern[k][1] / steps
+        logical = algo[k] / (ms / 1e3) / 1e9
+        e = {"ms_per_step": round(ms, 4), "node_visits": int(units[k]),
+             "logical_gbs": round(logical, 1), "logical_frac": round(logical / hbm, 4)}
+        m = ncu_metrics(k)
+        if m is not None and "dram_bytes_per_unit" in m:
+            dram = float(m["dram_bytes_per_unit"]) * units[k] / (ms / 1e3) / 1e9
+            e["dram_gbs"] = round(dram, 1)
+            e["dram_frac"] = round(dram / hbm, 4)
+        iss = issue_fraction([k], units[k], ms, clk)
+        if iss:
+            e["issue"] = iss
+        fr = {"hbm": e.get("dram_frac"), "issue": (iss or {}).get("frac")}
+        fr = {a: b for a, b in fr.items() if b is not None}
+        if fr:
+            e["bound"] = max(fr, key=fr.get)
+            e["frac"] = fr[e["bound"]]
+        out[k] = e
+    if not out:
+        return None
+    out["peak"] = hbm
+    out["peak_kind"] = peak_kind
+    out["note"] = ("dram from ncu DRAM bytes per node visit on the profile case (profiles/ncu_metrics.txt) "
+                   "scaled to this run's visits; issue = warp instructions per visit x visits over the "
+                   "kernel's issue slots; logical counts every node byte, most served by L2")
+    return out
+
+
+def ncu_metrics(kernel: str):
+    """Instruction and DRAM counters of `kernel` from the committed ncu
+    summary, if taken on the current source of that kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_metrics.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_sha(KERNEL_SOURCES.get(kernel, []))
+    for line in open(path):
+        kv = dict(re.findall(r"(\w+)=(\S+)", line))
+        if kv.get("kernel") == kernel:
+            return kv if kv.get("source_sha") == want else None
+    return None
+
+
+def issue_fraction(kernels, units, ms, clk, sms=152, schedulers=4):
+    """Issue-slot use of kernels that process `units` work units in `ms`:
+    instructions per unit (ncu, profile case) * units / (issue slots per
+    second * time).  Issue slots per second = SMs * 4 schedulers * the
+    median SM clock sampled during the timed region."""
+    inst_per_unit = 0.0
+    for k in kernels:
+        m = ncu_metrics(k)
+        if m is None or "inst_per_unit" not in m:
+            return None
+        inst_per_unit += float(m["inst_per_unit"])
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    slots = sms * schedulers * mhz * 1e6 * (ms / 1e3)
+    return {"inst_per_unit": round(inst_per_unit, 2), "units": int(units),
+            "frac": round(inst_per_unit * units / slots, 4), "sm_mhz": mhz,
+            "what": "warp instructions per work unit from ncu on the profile case, scaled to this run's "
+                    "units, over the issue slots of the kernels' time"}
 
 
 # ------------------------------------------------------------------- ours
@@ -269,17 +386,23 @@ def run_ours(args):
     # ---- pick fanout / layout / mapping / traversal order with the library's
     # autotuner (one build + sorted select per configuration, CUDA-event timed)
     fanouts = [args.fanout] if args.fanout else [16, 32, 64]
-    tune = rt.rtree_autotune(rects, queries, ids, fanouts=fanouts, include_build=True, stream=stream,
-                             orders=args.order != "input")
-    sweep = {k: v for k, v in tune["all"].items()
-             if (args.layout == "auto" or f"_{args.layout}_" in k)
-             and (args.mapping == "auto" or args.mapping in k)
-             and (args.order == "auto" or k.endswith("_hilbert") == (args.order == "hilbert"))}
-    best = min(sweep, key=sweep.get)
-    F = int(best.split("_")[0][1:])
-    layout = best.split("_")[1]
-    order = "hilbert" if best.endswith("_hilbert") else "input"
-    mapping = best[len(f"F{F}_{layout}_"):].replace("_hilbert", "")
+    if args.no_tune:
+        if not args.fanout or "auto" in (args.layout, args.mapping, args.order):
+            raise SystemExit("--no-tune needs --fanout, --layout, --mapping and --order")
+        F, layout, mapping, order = args.fanout, args.layout, args.mapping, args.order
+        sweep = None
+    else:
+        tune = rt.rtree_autotune(rects, queries, ids, fanouts=fanouts, include_build=True, stream=stream,
+                                 orders=args.order != "input")
+        sweep = {k: v for k, v in tune["all"].items()
+                 if (args.layout == "auto" or f"_{args.layout}_" in k)
+                 and (args.mapping == "auto" or args.mapping in k)
+                 and (args.order == "auto" or k.endswith("_hilbert") == (args.order == "hilbert"))}
+        best = min(sweep, key=sweep.get)
+        F = int(best.split("_")[0][1:])
+        layout = best.split("_")[1]
+        order = "hilbert" if best.endswith("_hilbert") else "input"
+        mapping = best[len(f"F{F}_{layout}_"):].replace("_hilbert", "")
     total_hits = step(F, layout, mapping, order)
 
     for _ in range(args.warmup):
@@ -322,17 +445,22 @@ def run_ours(args):
     persist = None if args.no_persist else run_persist(rt, torch, rects, ids, queries, F, layout, rank)
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
+    # share = the kernel's event time over the step's wall time (the sort's
+    # class kernels overlap one another, so their shares can add up past 1;
+    # sort_all is their span)
     breakdown = {}
-    total_ms = max(1e-9, sum(v[1] for v in kern.values()))
     for name, (n_l, ms) in kern.items():
         if n_l == 0:
             continue
         entry = {"launches": n_l, "ms_per_step": round(ms / args.steps, 3),
-                 "share": round(ms / total_ms, 4)}
+                 "share": round(ms / max(1e-9, ms_total), 4)}
         if name in algo and ms > 0:
             entry["gbs"] = round(algo[name] / (ms / args.steps / 1e3) / 1e9, 1)
         breakdown[name] = entry
-    dominant = max((k for k in kern if k in algo), key=lambda k: kern[k][1])
+    # the sort's class kernels overlap on side streams, so their event times
+    # are not additive: the sort counts as one unit timed by its span
+    overlapped = {"sort_warp", "sort_cta", "sort_gather", "sort_msd", "sort_bucket"} if "sort_all" in kern else set()
+    dominant = max((k for k in kern if k in algo and k not in overlapped), key=lambda k: kern[k][1])
     n_l, ms = kern[dominant]
     ms_step = ms / args.steps  # the kernel's time in one step, all its launches
     achieved = algo[dominant] / (ms_step / 1e3) / 1e9
@@ -345,24 +473,12 @@ def run_ours(args):
     if traffic_note:
         roofline["traffic_note"] = traffic_note
     if dominant.startswith("sort_"):
-        roofline["note"] = ("the CTA sort is bound by shared-memory work and per-segment latency, not by HBM: "
-                            "ncu shows 45-53% issue active, barrier and scoreboard stalls and a few % of DRAM peak "
-                            "(profiles/select_sort_kernels_profile_case.md)")
-    # the node-test kernels (count and descriptor passes) against the same peak
-    nt = [k for k in ("select_bound", "select_count", "select_desc") if k in kern and kern[k][0] > 0 and k in algo]
-    roofline_node_test = None
-    if nt:
-        nt_ms = sum(kern[k][1] for k in nt) / args.steps
-        nt_bytes = sum(algo[k] for k in nt)
-        nt_traffic = [ncu_traffic(k)[0] for k in nt]
-        roofline_node_test = {
-            "kernels": nt, "bound": "hbm", "achieved": round(nt_bytes / (nt_ms / 1e3) / 1e9, 1), "peak": hbm,
-            "unit": "GB/s", "frac": round(nt_bytes / (nt_ms / 1e3) / 1e9 / hbm, 4), "peak_kind": peak_kind,
-            "algorithmic_bytes_per_step": nt_bytes,
-            "traffic": None if any(t is None for t in nt_traffic) else sum(nt_traffic),
-            "note": "node bytes include upper tree levels served from L2, so frac can exceed 1; "
-                    "ncu: bound and count passes ~95% L2 hit and ~80% issue-active (bound by the node tests "
-                    "themselves)"}
+        roofline["note"] = ("sort_all = the whole segmented sort (warp, CTA and long-segment classes on side "
+                            "streams), wall time of its span; 8 B per id (gathered + written), 24 B more per id of "
+                            "segments over 40960; bound by shared-memory work and per-segment latency, not by HBM "
+                            "(ncu: 45-53% issue active, a few % of DRAM peak)")
+    # the node-test kernels, each against HBM (ncu DRAM bytes) and issue slots
+    roofline_node_test = node_test_roofline(kern, algo, stats, args.steps, hbm, peak_kind, clk)
 
     # ---- end to end through the C ABI with host (pinned) buffers
     e2e = None
@@ -456,18 +572,27 @@ def run_ours(args):
             rt.rtree_timing_enable(False)
             k = rt.rtree_timing_get()
             trav = sum(v[1] for n, v in k.items() if n.startswith("join_"))
-            return pairs, ms, trav
+            return pairs, ms, trav, {n: v for n, v in k.items() if n.startswith("join_") and v[0]}
 
-        pairs, jms, jtrav = jtime()
-        ppairs, pms, ptrav = jtime(sort_children=True, prune="on")
+        pairs, jms, jtrav, jk = jtime()
+        ppairs, pms, ptrav, pk = jtime(sort_children=True, prune="on")
         assert ppairs == pairs
+        a = rt.RTree(jr, None, fanout=32, stream=stream, sort_children=True)
+        b = rt.RTree(js, None, fanout=32, stream=stream, sort_children=True)
+        jstats = a.join_stats(b, stream=stream, prune="off")
+        a.close(); b.close()
         join = {"metric": "join pairs/s (2M x 2M, build of both trees included)",
                 "value": round(pairs * world / (jms / 1e3), 1), "unit": "pairs/s",
                 "pairs": int(pairs), "ms_per_step": round(jms, 3),
                 "traversal_ms": round(jtrav, 3),
+                "join_stats": jstats,
+                "roofline": join_roofline(jstats, 32, 32, jk, hbm, peak_kind, clk),
                 "pruned": {"what": "sorted-children trees, O3 + O4/O5 pruned join (Section 4.2)",
                            "value": round(ppairs * world / (pms / 1e3), 1), "unit": "pairs/s",
-                           "ms_per_step": round(pms, 3), "traversal_ms": round(ptrav, 3)}}
+                           "ms_per_step": round(pms, 3), "traversal_ms": round(ptrav, 3),
+                           "roofline": join_roofline(jstats, 32, 32, pk, hbm, peak_kind, clk)}}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            join["cpu_baseline"] = oracle_join_rate(j, 32)
 
     # ---- CPU oracle baseline (rank 0, one GPU runs only)
     cpu = None
@@ -712,21 +837,84 @@ def run_serve(args, rt, dg, torch, dev, rank, world, F, layout):
 
 
 # ------------------------------------------------------------- reference
-def oracle_rate(w, F, sample=CPU_SAMPLE_QUERIES, build_s=None, steps=1):
+def cpu_info():
+    """Host CPU as the OS reports it (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip().lower() in ("model name", "model"):
+                if v.strip() and not v.strip().isdigit():
+                    model = v.strip()
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                k, _, v = line.partition(":")
+                if k.strip().lower() in ("model name", "cpu part"):
+                    model = v.strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def oracle_rate(w, F, sample=CPU_SAMPLE_QUERIES):
+    """The CPU oracle on this host: STR build of all rectangles (one thread),
+    then a sorted select of a fixed subset of the queries, once on one
+    thread and once on every core; extrapolated to the whole batch."""
     import oracle
+    threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     tree = oracle.Tree(w.rects, w.ids, F)
-    tb = time.perf_counter() - t0 if build_s is None else build_s
+    tb = time.perf_counter() - t0
     qs = w.queries[:sample]
     t1 = time.perf_counter()
-    for _ in range(steps):
-        tree.select(qs)
-    per_q = (time.perf_counter() - t1) / (steps * qs.shape[0])
+    tree.select(qs, threads=1)
+    per_q1 = (time.perf_counter() - t1) / qs.shape[0]
+    t1 = time.perf_counter()
+    tree.select(qs, threads=threads)
+    per_qn = (time.perf_counter() - t1) / qs.shape[0]
     Q = w.queries.shape[0]
-    return {"value": round(Q / (tb + per_q * Q), 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle STR build of all {w.rects.shape[0]} rects ({tb:.2f} s) + sorted select "
-                      f"of the first {qs.shape[0]} queries ({per_q * 1e6:.1f} us/query), extrapolated "
-                      f"to {Q} queries: {Q} / (build + per_query * {Q})"}
+    return {"value": round(Q / (tb + per_qn * Q), 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"oracle STR build of all {w.rects.shape[0]} rects at F={F} ({tb:.2f} s, one thread) + "
+                      f"sorted select of the first {qs.shape[0]} queries on {threads} threads "
+                      f"({per_qn * 1e6:.2f} us/query), extrapolated to {Q} queries: "
+                      f"{Q} / (build + per_query * {Q})",
+            "build_s": round(tb, 3),
+            "select_qps": {"threads_1": round(1.0 / per_q1, 1), f"threads_{threads}": round(1.0 / per_qn, 1)},
+            "single_thread": {"value": round(Q / (tb + per_q1 * Q), 2), "cores": 1,
+                              "per_query_us": round(per_q1 * 1e6, 2)},
+            "cpu": cpu_info()}
+
+
+def oracle_join_rate(j, F=32):
+    """The CPU oracle's join of the join workload: both STR builds (one
+    thread each) + the synchronized traversal on one thread and on every
+    core; pairs/s over builds + traversal, as the GPU step counts them."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    a = oracle.Tree(j.rects, j.ids, F)
+    b = oracle.Tree(j.rects_s, j.ids_s, F)
+    tb = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    p1 = a.join(b, threads=1)
+    tj1 = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    pn = a.join(b, threads=threads)
+    tjn = time.perf_counter() - t1
+    assert np.array_equal(p1, pn)
+    pairs = len(pn)
+    return {"value": round(pairs / (tb + tjn), 1), "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "sample": f"the whole join workload: STR builds of R and S ({tb:.2f} s, one thread) + join "
+                      f"on {threads} threads ({tjn:.2f} s); pairs / (builds + join)",
+            "pairs": int(pairs), "build_s": round(tb, 3),
+            "single_thread": {"value": round(pairs / (tb + tj1), 1), "cores": 1, "join_s": round(tj1, 3)},
+            "join_s": round(tjn, 3), "cpu": cpu_info()}
 
 
 def run_reference(args):
@@ -736,23 +924,26 @@ def run_reference(args):
     from paper_2309_16913_gb300 import datagen as dg
     import oracle
     w = dg.workload(WORKLOAD, seed=1, n=args.n, q=args.q)
-    F = args.fanout or 16
+    F = args.fanout or REF_FANOUT
+    threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     tree = oracle.Tree(w.rects, w.ids, F)
     tb = time.perf_counter() - t0
     qs = w.queries[:CPU_SAMPLE_QUERIES]
     for _ in range(args.warmup):
-        tree.select(qs)
+        tree.select(qs, threads=threads)
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        tree.select(qs)
+        tree.select(qs, threads=threads)
     el = time.perf_counter() - t1
     per_q = el / (args.steps * qs.shape[0])
     Q = w.queries.shape[0]
     value = Q / (tb + per_q * Q)
-    cpu = {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"tree built once ({tb:.2f} s); each step = sorted select of the first "
-                     f"{qs.shape[0]} of {Q} queries; value = {Q} / (build + per_query * {Q})"}
+    cpu = {"value": round(value, 2), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"tree built once at F={F} ({tb:.2f} s, one thread); each step = sorted select "
+                     f"of the first {qs.shape[0]} of {Q} queries on {threads} threads; "
+                     f"value = {Q} / (build + per_query * {Q})",
+           "cpu": cpu_info()}
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),

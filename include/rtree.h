@@ -435,6 +435,17 @@ typedef struct rtree_join_opts {
 RTREE_API rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s, const rtree_join_opts_t *opts,
                                      void *stream, rtree_result_t **out);
 
+/*
+ * rtree_join_stats -- runs rtree_join_ex and, instead of the pairs, returns
+ * the traversal's counters: stats[0] node pairs tested with both trees at
+ * the same internal level, [1] node pairs where only r descends (r taller),
+ * [2] where only s descends, [3] leaf node pairs, [4] pairs found; [5..7]
+ * are 0.  Used to turn the join kernels' times into bytes and tests per
+ * second.  Errors: as rtree_join_ex, and RTREE_EINVAL for NULL stats.
+ */
+RTREE_API rtree_status rtree_join_stats(const rtree_t *r, const rtree_t *s, const rtree_join_opts_t *opts,
+                                        void *stream, int64_t stats[8]);
+
 /* Result accessors.  Pointers are device pointers owned by the result. */
 RTREE_API int64_t rtree_result_total(const rtree_result_t *res);         /* ids (select) or pairs (join) */
 RTREE_API int64_t rtree_result_rows(const rtree_result_t *res);          /* q for select, 0 for join */
@@ -524,6 +535,17 @@ RTREE_API long long rtree_launch_count(void);
  * RTREE_ENOMEM (k = 0: the next one); k < 0 disables.  The failure is made
  * on the host, before cudaMallocAsync is called; no GPU fault is involved. */
 RTREE_API void rtree_debug_fail_alloc_after(long long k);
+
+/* Testing hook for the bounded waits of the work-queue mapping
+ * (RTREE_MAP_WORK_QUEUE): the next work-queue pass launched by any host
+ * thread limits each device-side wait for work to `cycles` GPU clock cycles
+ * (<= 0: the default, about one second), and with hold != 0 it counts one
+ * work item that is never published, so the pass cannot end by running out
+ * of work: every waiting warp's wait runs out, the warp records the timeout
+ * and returns, and the call reports RTREE_ETIMEOUT.  The waits end by
+ * themselves; no GPU fault or trap is involved and the context stays usable.
+ * The setting applies to one pass, then resets. */
+RTREE_API void rtree_debug_wq_wait(long long cycles, int hold);
 
 #ifdef __cplusplus
 }

@@ -485,8 +485,33 @@ rtree_status rtree_join(const rtree_t *r, const rtree_t *s_tree, void *stream, r
     return rtree_join_ex(r, s_tree, nullptr, stream, out);
 }
 
+namespace {
+rtree_status join_impl(const rtree_t *r, const rtree_t *s_tree, const rtree_join_opts_t *opts,
+                       void *stream, rtree_result_t **out, int64_t *stats);
+}
+
 rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s_tree, const rtree_join_opts_t *opts,
                            void *stream, rtree_result_t **out)
+{
+    return join_impl(r, s_tree, opts, stream, out, nullptr);
+}
+
+rtree_status rtree_join_stats(const rtree_t *r, const rtree_t *s_tree, const rtree_join_opts_t *opts,
+                              void *stream, int64_t stats[8])
+{
+    if (!stats)
+        return fail(RTREE_EINVAL, "rtree_join_stats: stats is NULL");
+    for (int i = 0; i < 8; ++i)
+        stats[i] = 0;
+    rtree_result_t *res = nullptr;
+    const rtree_status st = join_impl(r, s_tree, opts, stream, &res, stats);
+    rtree_result_free(res);
+    return st;
+}
+
+namespace {
+rtree_status join_impl(const rtree_t *r, const rtree_t *s_tree, const rtree_join_opts_t *opts,
+                       void *stream, rtree_result_t **out, int64_t *stats)
 {
     clear_error();
     if (!out)
@@ -507,7 +532,7 @@ rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s_tree, const rtree_
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         rtree_result *res = new rtree_result();
         res->device = r->device;
-        rtree_status st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res);
+        rtree_status st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res, stats);
         if (st == RTREE_OK) {
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess)
@@ -526,6 +551,7 @@ rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s_tree, const rtree_
         return fail(RTREE_ENOMEM, "rtree_join: host allocation failed");
     }
 }
+}  // namespace
 
 int64_t rtree_result_total(const rtree_result_t *r) { return r ? r->total : 0; }
 int64_t rtree_result_rows(const rtree_result_t *r) { return r ? r->rows : 0; }

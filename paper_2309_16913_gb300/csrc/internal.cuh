@@ -108,6 +108,21 @@ class KernelTimer {
     int entry_ = 0;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+// Times a span of work on stream s under `name` (events on s at both ends)
+// without counting it as a kernel launch; for spans whose kernels run
+// concurrently on several streams, where per-kernel times overlap.
+class PhaseTimer {
+  public:
+    PhaseTimer(const char *name, cudaStream_t s);
+    ~PhaseTimer();
+    PhaseTimer(const PhaseTimer &) = delete;
+    PhaseTimer &operator=(const PhaseTimer &) = delete;
+
+  private:
+    cudaStream_t s_;
+    int entry_ = 0;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 // Resolves recorded event pairs into totals (call after a stream sync).
 void timing_resolve();
 // Graph capture on this thread: launches are counted, not timed; each replay
@@ -409,8 +424,11 @@ rtree_status select_stats(const rtree *t, const float4 *queries, int64_t q, cuda
 
 // R-tree join of two trees on the same device; prune selects the sorted-node
 // kernel for equal-height pairs (both trees must have sorted children).
+// stats (optional, 8 zeroed words) receives node pairs tested at equal
+// internal heights [0], with only R descending [1], only S descending [2],
+// at the leaves [3], and the pairs found [4].
 rtree_status tree_join(const rtree *r, const rtree *s_tree, bool prune, cudaStream_t s,
-                       rtree_result *res);
+                       rtree_result *res, int64_t *stats = nullptr);
 
 }  // namespace rt
 

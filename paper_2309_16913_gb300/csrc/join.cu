@@ -304,7 +304,7 @@ rtree_status sort_pairs(int2 *pairs, int64_t n, cudaStream_t s)
 }  // namespace
 
 rtree_status tree_join(const rtree *R, const rtree *S, bool prune, cudaStream_t s,
-                       rtree_result *res)
+                       rtree_result *res, int64_t *stats)
 {
     res->rows = 0;
     res->total = 0;
@@ -326,6 +326,8 @@ rtree_status tree_join(const rtree *R, const rtree *S, bool prune, cudaStream_t 
     for (;;) {
         const int ra = R->levels - 1 - da, rb = S->levels - 1 - db;
         const int mode = (ra == 0 && rb == 0) ? J_LEAF : (ra > rb ? J_A : (rb > ra ? J_B : J_BOTH));
+        if (stats)
+            stats[mode] += np;  // node pairs tested in this mode
         DevBuf<int32_t> cnt(s);
         DevBuf<int64_t> off(s);
         RT_TRY(cnt.alloc(np, "join counts"));
@@ -349,6 +351,8 @@ rtree_status tree_join(const rtree *R, const rtree *S, bool prune, cudaStream_t 
             RT_LAUNCH();
         }
         if (mode == J_LEAF || total == 0) {
+            if (stats)
+                stats[4] = mode == J_LEAF ? total : 0;
             RT_TRY(sort_pairs(next.p, total, s));
             RT_CUDA(cudaStreamSynchronize(s));
             res->total = total;

@@ -58,7 +58,10 @@ rtree_status scratch_address(int dev, unsigned char **out)
     return RTREE_OK;
 }
 
-bool is_device_memory(const void *p)
+// True if p is device (or managed) memory that the kernels on `dev` can
+// address directly: memory of another GPU is refused, since reaching it
+// would need peer access.
+bool is_device_memory_on(const void *p, int dev)
 {
     cudaPointerAttributes a;
     memset(&a, 0, sizeof(a));
@@ -66,7 +69,9 @@ bool is_device_memory(const void *p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged)
+        return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Exclusive scan of at most kNoallocMaxQueries counts by one block;
@@ -146,10 +151,10 @@ extern "C" rtree_status rtree_range_select_noalloc(const rtree_t *t, const float
                     (long long)q, (long long)kNoallocMaxQueries);
     if (capacity < 0 || !offsets || (capacity > 0 && !ids) || (q > 0 && !queries))
         return fail(RTREE_EINVAL, "rtree_range_select_noalloc: NULL buffer or negative capacity");
-    if (!is_device_memory(offsets) || (q > 0 && !is_device_memory(queries)) ||
-        (capacity > 0 && !is_device_memory(ids)))
+    if (!is_device_memory_on(offsets, t->device) || (q > 0 && !is_device_memory_on(queries, t->device)) ||
+        (capacity > 0 && !is_device_memory_on(ids, t->device)))
         return fail(RTREE_EINVAL, "rtree_range_select_noalloc: queries, offsets and ids must be "
-                                  "device memory");
+                                  "device memory on the tree's device (%d)", t->device);
     if ((reinterpret_cast<uintptr_t>(queries) & 15) || (reinterpret_cast<uintptr_t>(offsets) & 7) ||
         (reinterpret_cast<uintptr_t>(ids) & 3))
         return fail(RTREE_EINVAL, "rtree_range_select_noalloc: queries must be 16-byte aligned, "

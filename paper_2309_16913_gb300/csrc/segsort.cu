@@ -1170,6 +1170,8 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
         out_cap = total;
     if (nseg >= (int64_t)INT32_MAX)
         return fail(RTREE_EOVERFLOW, "too many segments to sort (%lld)", (long long)nseg);
+    // the whole sort, all classes, as one span (its kernels overlap)
+    PhaseTimer span_("sort_all", s);
     // Every list length stays on the device; the launches below are sized
     // by upper bounds and read the actual lengths themselves, so the whole
     // sort is enqueued without a host round trip.

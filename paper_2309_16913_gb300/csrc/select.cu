@@ -33,6 +33,7 @@
 //   DESC     writes the leaf hits and, for every whole subtree, its (lo, hi)
 //            range of the tree's id array; the sorted output is then built
 //            by the segmented sort, which reads the ranges directly.
+#include <atomic>
 #include <cstring>
 
 #include "internal.cuh"
@@ -344,10 +345,17 @@ struct WorkQueue {
     unsigned long long *head;
     unsigned long long *tail;
     long long *pending;
+    long long wait_cycles;  // limit of one wait, in GPU clock cycles
 };
 
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr long long kWaitCycles = 2000000000LL;  // about one second
+
+// Test hook (rtree_debug_wq_wait): the next work-queue launch waits at most
+// g_dbg_wait_cycles and, with g_dbg_hold, counts one item that is never
+// published.
+std::atomic<long long> g_dbg_wait_cycles{0};
+std::atomic<int> g_dbg_hold{0};
 
 __device__ __forceinline__ unsigned long long pack_item(int q, int node)
 {
@@ -386,7 +394,7 @@ __global__ void __launch_bounds__(kThreads)
                     break;
                 if (*pend == 0)
                     break;
-                if (clock64() - t0 > kWaitCycles) {
+                if (clock64() - t0 > wq.wait_cycles) {
                     atomicOr(flags, FLAG_TIMEOUT);
                     break;
                 }
@@ -481,8 +489,10 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// hold: items counted as pending but never published (0 in normal use).
 __global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap, int64_t Q,
-                          unsigned long long *__restrict__ ctl, const uint32_t *__restrict__ order)
+                          unsigned long long *__restrict__ ctl, const uint32_t *__restrict__ order,
+                          int hold)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cap;
          i += (long long)gridDim.x * blockDim.x)
@@ -490,7 +500,7 @@ __global__ void k_wq_init(unsigned long long *__restrict__ items, long long cap,
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl[0] = 0;                        // head
         ctl[1] = (unsigned long long)Q;    // tail
-        ctl[2] = (unsigned long long)Q;    // pending
+        ctl[2] = (unsigned long long)(Q + hold);  // pending
     }
 }
 
@@ -638,13 +648,17 @@ rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, con
         items_p = items.p;
         ctl_p = ctl.p;
     }
+    const long long dbg_wait = g_dbg_wait_cycles.exchange(0);
+    const int dbg_hold = g_dbg_hold.exchange(0);
     {
         KernelTimer kt_("wq_init", s);
         int64_t b = (cap_items + 255) / 256;
-        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items_p, cap_items, Q, ctl_p, io.order);
+        k_wq_init<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(items_p, cap_items, Q, ctl_p, io.order,
+                                                                   dbg_hold ? 1 : 0);
         RT_LAUNCH();
     }
-    WorkQueue wq{items_p, cap_items, ctl_p, ctl_p + 1, reinterpret_cast<long long *>(ctl_p + 2)};
+    WorkQueue wq{items_p, cap_items, ctl_p, ctl_p + 1, reinterpret_cast<long long *>(ctl_p + 2),
+                 dbg_wait > 0 ? dbg_wait : kWaitCycles};
     {
         KernelTimer kt_(pass == PASS_COUNT ? "select_count" : pass == PASS_SCATTER ? "select_scatter" : "select_desc", s);
         kern<<<(unsigned)grid, kThreads, smem, s>>>(t->view(), q, Q, io, wq, flags, cap, stats);
@@ -1263,3 +1277,9 @@ rtree_status select_stats(const rtree *t, const float4 *queries, int64_t Q, cuda
 }
 
 }  // namespace rt
+
+extern "C" void rtree_debug_wq_wait(long long cycles, int hold)
+{
+    rt::g_dbg_wait_cycles.store(cycles > 0 ? cycles : 0);
+    rt::g_dbg_hold.store(hold != 0);
+}

@@ -121,6 +121,30 @@ KernelTimer::~KernelTimer()
     g_pending.push_back(Pending{entry_, a_, b_});
 }
 
+PhaseTimer::PhaseTimer(const char *name, cudaStream_t s) : s_(s)
+{
+    if (t_capture_launches >= 0)
+        return;
+    std::lock_guard<std::mutex> g(g_mu);
+    entry_ = entry_for(name);
+    g_entries[entry_].launches++;  // counts spans, not kernel launches
+    if (g_enabled) {
+        a_ = get_event();
+        b_ = get_event();
+        if (a_ && b_)
+            cudaEventRecord(a_, s_);
+    }
+}
+
+PhaseTimer::~PhaseTimer()
+{
+    if (!a_ || !b_)
+        return;
+    std::lock_guard<std::mutex> g(g_mu);
+    cudaEventRecord(b_, s_);
+    g_pending.push_back(Pending{entry_, a_, b_});
+}
+
 void timing_resolve()
 {
     std::lock_guard<std::mutex> g(g_mu);

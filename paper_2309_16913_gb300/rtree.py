@@ -106,6 +106,7 @@ def _bind(lib):
         "rtree_range_select": (C.c_int, [vp, vp, i64, C.POINTER(rtree_select_opts_t), vp, C.POINTER(vp)]),
         "rtree_join": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
         "rtree_join_ex": (C.c_int, [vp, vp, vp, vp, C.POINTER(vp)]),
+        "rtree_join_stats": (C.c_int, [vp, vp, vp, vp, C.POINTER(C.c_int64)]),
         "rtree_save": (C.c_int, [vp, C.c_char_p, vp]),
         "rtree_range_select_host": (C.c_int, [vp, vp, C.c_int64, vp, vp, vp, vp, C.c_int64,
                                               C.POINTER(C.c_int64)]),
@@ -124,6 +125,7 @@ def _bind(lib):
         "rtree_last_error": (C.c_char_p, []),
         "rtree_version": (C.c_char_p, []),
         "rtree_debug_fail_alloc_after": (None, [C.c_longlong]),
+        "rtree_debug_wq_wait": (None, [C.c_longlong, C.c_int]),
         "rtree_plan_create": (C.c_int, [vp, i64, i64, C.POINTER(rtree_select_opts_t), C.POINTER(vp)]),
         "rtree_plan_run": (C.c_int, [vp, vp, i64, vp, C.POINTER(C.c_int64)]),
         "rtree_plan_offsets": (vp, [vp]),
@@ -429,6 +431,17 @@ def rtree_join_ex(r_handle: int, s_handle: int, prune: str | int = "auto", strea
     return out.value
 
 
+def rtree_join_stats(r_handle: int, s_handle: int, prune: str | int = "auto", stream=None) -> dict:
+    """Traversal counters of one join (the pairs themselves are dropped)."""
+    lib = load_library()
+    opts = rtree_join_opts_t()
+    opts.prune = PRUNES[prune] if isinstance(prune, str) else int(prune)
+    st = (C.c_int64 * 8)()
+    _check(lib.rtree_join_stats(r_handle, s_handle, C.byref(opts), _stream(stream), st), lib)
+    keys = ("pairs_equal_internal", "pairs_r_descends", "pairs_s_descends", "pairs_leaf", "pairs_found")
+    return {k: int(st[i]) for i, k in enumerate(keys)}
+
+
 def rtree_result_total(res: int) -> int:
     return load_library().rtree_result_total(res)
 
@@ -472,6 +485,10 @@ def rtree_version() -> str:
 
 def rtree_debug_fail_alloc_after(k: int) -> None:
     load_library().rtree_debug_fail_alloc_after(int(k))
+
+
+def rtree_debug_wq_wait(cycles: int, hold: bool = True) -> None:
+    load_library().rtree_debug_wq_wait(int(cycles), 1 if hold else 0)
 
 
 def rtree_plan_create(handle: int, max_queries: int, max_ids: int, mapping: str | int = "auto") -> int:
@@ -782,3 +799,6 @@ class RTree:
         if prune is None:
             return Result(rtree_join(self.handle, other.handle, stream))
         return Result(rtree_join_ex(self.handle, other.handle, prune, stream))
+
+    def join_stats(self, other: "RTree", stream=None, prune: str | int = "auto") -> dict:
+        return rtree_join_stats(self.handle, other.handle, prune, stream)

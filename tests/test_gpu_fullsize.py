@@ -1,13 +1,17 @@
 """Full-size parity at the benchmark's workloads, in the benchmark's launch
 configuration (the same C ABI calls bench.py times).
 
-The oracle cannot walk a million queries in seconds, so at 10M rectangles
-every query is checked for properties that hold at any size (offsets are a
-valid CSR, each id list strictly ascending and within the id range, the sum
-of counts equals the total) and a seeded sample of queries, including every
-heavy query of the uneven mix, is compared exactly with the oracle.  The
-2M x 2M join is compared in full.
+At 10M rectangles every one of the million queries is compared exactly with
+the oracle, whose select runs on all host cores (orc_select_mt), in chunks
+of 65536 queries: at the benchmark's configuration (F=64, AoS, Hilbert
+order) and at F=16 SoA in input order; the uneven mix (100k queries, 1%
+heavy) is compared in full too.  The remaining fanout/layout pairs are
+checked for properties that hold at any size (a valid CSR, strictly
+ascending id lists within the id range) and on a seeded sample.  The
+2M x 2M join is compared in full, plain and with the sorted-node prunings.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -48,6 +52,47 @@ def check_sample(rt, t_gpu, t_orc, queries, sample, F):
         res.close()
 
 
+THREADS = os.cpu_count() or 1
+CHUNK = 65536
+
+
+def compare_all(t_gpu, t_orc, queries, context, **select_kw):
+    """Every query of the batch equal to the oracle (chunked)."""
+    import torch
+    q = torch.from_numpy(queries).cuda()
+    res = t_gpu.range_select(q, **select_kw)
+    try:
+        off = res.offsets_tensor().cpu().numpy()
+        ids_dev = res.ids_tensor()
+        Q = queries.shape[0]
+        for c0 in range(0, Q, CHUNK):
+            c1 = min(Q, c0 + CHUNK)
+            o_off, o_ids = t_orc.select(queries[c0:c1], threads=THREADS)
+            g_off = off[c0:c1 + 1] - off[c0]
+            if not np.array_equal(g_off, o_off):
+                bad = c0 + int(np.nonzero(np.diff(g_off) != np.diff(o_off))[0][0])
+                raise AssertionError(f"{context}: count of query {bad} differs")
+            got = ids_dev[off[c0]:off[c1]].cpu().numpy()
+            if not np.array_equal(got, o_ids):
+                k = int(np.nonzero(got != o_ids)[0][0])
+                qi = c0 + int(np.searchsorted(o_off, k, side="right") - 1)
+                raise AssertionError(f"{context}: ids of query {qi} differ")
+        return int(off[-1])
+    finally:
+        res.close()
+
+
+@pytest.mark.parametrize("F,layout,order", [(64, "aos", "hilbert"), (16, "soa", "input")])
+def test_scaled_10m_every_query_exact(rt, F, layout, order):
+    import torch
+    w = dg.workload("scaled")
+    t_orc = oracle.Tree(w.rects, w.ids, F)
+    with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(),
+                  fanout=F, layout=layout) as t:
+        total = compare_all(t, t_orc, w.queries, f"F={F} {layout} {order}", order=order)
+    assert total > 10**9
+
+
 @pytest.mark.parametrize("F", [16, 32, 64])
 def test_scaled_10m_1m_queries(rt, F):
     import torch
@@ -62,23 +107,20 @@ def test_scaled_10m_1m_queries(rt, F):
         assert total > 10**8
 
 
-def test_uneven_10m_with_heavy_queries(rt):
+def test_uneven_10m_every_query_exact(rt):
     import torch
     w = dg.workload("uneven")
-    sizes = (w.queries[:, 2] - w.queries[:, 0]) * (w.queries[:, 3] - w.queries[:, 1])
-    heavy = np.nonzero(sizes > 0.05 * 0.05)[0]
-    rng = np.random.default_rng(7)
-    sample = np.sort(np.concatenate([rng.choice(heavy, min(150, heavy.size), replace=False),
-                                     rng.choice(w.queries.shape[0], 600, replace=False)]))
-    sample = np.unique(sample)
     t_orc = oracle.Tree(w.rects, w.ids, 16)
+    sizes = (w.queries[:, 2] - w.queries[:, 0]) * (w.queries[:, 3] - w.queries[:, 1])
+    assert np.count_nonzero(sizes > 0.05 * 0.05) > 500
     with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(), fanout=16) as t:
-        check_sample(rt, t, t_orc, w.queries, sample, 16)
+        for mapping in ("warp_per_query", "work_queue"):
+            compare_all(t, t_orc, w.queries, f"uneven {mapping}", mapping=mapping)
 
 
 def test_join_2m_x_2m_full(rt):
     w = dg.workload("join")
-    want = oracle.Tree(w.rects, w.ids, 32).join(oracle.Tree(w.rects_s, w.ids_s, 32))
+    want = oracle.Tree(w.rects, w.ids, 32).join(oracle.Tree(w.rects_s, w.ids_s, 32), threads=THREADS)
     import torch
     with rt.RTree(torch.from_numpy(w.rects).cuda(), None, fanout=32) as a, \
             rt.RTree(torch.from_numpy(w.rects_s).cuda(), None, fanout=32) as b:
@@ -86,6 +128,13 @@ def test_join_2m_x_2m_full(rt):
         _, got = res.to_numpy()
         res.close()
     assert np.array_equal(got, want) and len(want) > 10**5
+    # the sorted-node prunings (O3, O4/O5) on sorted-children trees: same pairs
+    with rt.RTree(torch.from_numpy(w.rects).cuda(), None, fanout=32, sort_children=True) as a, \
+            rt.RTree(torch.from_numpy(w.rects_s).cuda(), None, fanout=32, sort_children=True) as b:
+        res = a.join(b, prune="on")
+        _, got = res.to_numpy()
+        res.close()
+    assert np.array_equal(got, want)
 
 
 def test_scaled_10m_host_results_pipelined(rt):

@@ -81,3 +81,19 @@ def test_self_join_diagonal(rt):
     got = join_gpu(rt, r, rid, r, rid, 8, 16)
     assert np.array_equal(got, oracle.brute_join(r, r, rid, rid))
     assert np.array_equal(got[got[:, 0] == got[:, 1]][:, 0], rid)
+
+
+def test_join_stats_counts(rt):
+    """rtree_join_stats: the pairs found equal the oracle's; the pruned join
+    visits exactly the same node pairs (its prunings skip only tests whose
+    pairs do not qualify); unequal heights show up as one-sided descents."""
+    w = dg.workload("join", n=200_000)
+    want = oracle.Tree(w.rects, w.ids, 8).join(oracle.Tree(w.rects_s, w.ids_s, 32))
+    with rt.RTree(w.rects, w.ids, fanout=8, sort_children=True) as a, \
+            rt.RTree(w.rects_s, w.ids_s, fanout=32, sort_children=True) as b:
+        plain = a.join_stats(b, prune="off")
+        pruned = a.join_stats(b, prune="on")
+    assert plain["pairs_found"] == len(want) > 5000
+    assert plain == pruned
+    assert plain["pairs_r_descends"] > 0 and plain["pairs_s_descends"] == 0  # R (F=8) is taller
+    assert plain["pairs_leaf"] >= plain["pairs_found"] / (8 * 32)

@@ -1,4 +1,5 @@
-"""The non-allocating range select, checked against the regular entry point.
+"""The non-allocating range select, checked against the CPU oracle and the
+regular entry point.
 
 rtree_range_select_noalloc exists for callers that cannot allocate device
 memory while running (an application that keeps all GPU memory in its own
@@ -12,6 +13,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import gpu_ready
 from paper_2309_16913_gb300 import datagen as dg
 
@@ -25,26 +27,40 @@ def _call(lib, handle, q, off, out, stream):
     return rc, total.value
 
 
-def test_noalloc_matches_range_select_on_two_calls():
+def test_noalloc_matches_oracle_and_range_select_on_two_calls():
     import torch
     rt = gpu_ready()
     lib = rt.load_library()
     stream = torch.cuda.current_stream().cuda_stream
     w = dg.workload("scaled", n=300_000, q=20_000)
     a, b = w.queries[:12_000], w.queries[12_000:]
+    t_orc = oracle.Tree(w.rects, w.ids, 16)
     with rt.RTree(torch.from_numpy(w.rects).cuda(), torch.from_numpy(w.ids).cuda(), fanout=16) as t:
         for qs in (a, b):  # two calls in a row share the library's fixed scratch
             qd = torch.from_numpy(np.ascontiguousarray(qs)).cuda()
             res = t.range_select(qd, unsorted=True)
             want_off, want_ids = res.to_numpy()
             res.close()
+            o_off, o_ids = t_orc.select(qs)
             off = torch.full((qd.shape[0] + 1,), -7, dtype=torch.int64, device="cuda")
             out = torch.full((int(want_off[-1]) + 100,), -7, dtype=torch.int32, device="cuda")
-            rc, total = _call(lib, t.handle, qd, off, out, stream)
+            torch.cuda.synchronize()
+            # any device allocation inside the call would now fail with RTREE_ENOMEM
+            lib.rtree_debug_fail_alloc_after(0)
+            try:
+                rc, total = _call(lib, t.handle, qd, off, out, stream)
+            finally:
+                lib.rtree_debug_fail_alloc_after(-1)
             assert rc == rt.RTREE_OK, rt.rtree_last_error()
-            assert total == want_off[-1]
-            assert np.array_equal(off.cpu().numpy(), want_off)
-            assert np.array_equal(out[:total].cpu().numpy(), want_ids)
+            assert total == want_off[-1] == o_off[-1]
+            got_off = off.cpu().numpy()
+            assert np.array_equal(got_off, want_off) and np.array_equal(got_off, o_off)
+            got = out[:total].cpu().numpy()
+            assert np.array_equal(got, want_ids)
+            # traversal order within a query; sorted, each query equals the oracle's list
+            for i in range(qs.shape[0]):
+                seg = np.sort(got[got_off[i]:got_off[i + 1]])
+                assert np.array_equal(seg, o_ids[o_off[i]:o_off[i + 1]]), f"query {i}"
             assert bool((out[total:] == -7).all())
 
 
