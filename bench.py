@@ -376,11 +376,15 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     def step(F, layout, mapping, order="input"):
+        # stream-ordered: the build and the select return once their work is
+        # enqueued (after the host reads they need), and the result and tree
+        # are released in the stream's order, so the host enqueues the next
+        # step while this one's sort still runs
         t = rt.RTree(rects, ids, fanout=F, layout=layout, stream=stream)
         res = t.range_select(queries, mapping=mapping, stream=stream, order=order)
         total = res.total
-        res.close()
-        t.close()
+        res.close(stream)
+        t.close(stream)
         return total
 
     # ---- pick fanout / layout / mapping / traversal order with the library's

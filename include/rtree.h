@@ -21,8 +21,19 @@
  * aligned are copied too).
  *
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
- * stream).  Every call below returns only after its device work on that stream
- * has finished, so results may be read as soon as a call returns RTREE_OK.
+ * stream).  rtree_build and rtree_range_select are stream-ordered: they
+ * return once their work is enqueued on `stream`, after the one host read
+ * each needs (the build's input check, the select's result sizes and total),
+ * and their outputs may be used by later work on that stream, or by the
+ * host once the stream has been synchronized (rtree_result_wait does that
+ * and also reports device-side errors of the work still in flight).  The
+ * other calls return only after their device work on `stream` has finished.
+ *
+ * Device memory.  A tree is built with an optional allocator
+ * (rtree_allocator_t); every device buffer the library allocates for that
+ * tree -- the tree itself, the scratch of calls on it, and their results --
+ * is taken from it and given back to it.  NULL selects cudaMallocAsync and
+ * cudaFreeAsync on the call's stream (the device's default memory pool).
  *
  * Errors.  Every call returns an rtree_status; on failure no output is
  * produced (output handles are set to NULL) and rtree_last_error() describes
@@ -119,6 +130,23 @@ typedef struct rtree_info {
 } rtree_info_t;
 
 /*
+ * Device-memory hook.  alloc(bytes, stream, ctx) returns device memory of
+ * the tree's device usable by work enqueued on `stream` after the call (or
+ * NULL on failure, which the library reports as RTREE_ENOMEM); free(p,
+ * stream, ctx) gives it back, usable again once the work enqueued on
+ * `stream` before the call has finished.  `stream` is a cudaStream_t as void*
+ * (NULL = legacy default stream).  The functions may be called from any host
+ * thread that calls into the library with this tree (serving workers
+ * included), and `ctx` must stay valid until the tree and all its results
+ * are freed.  The library copies the struct at rtree_build.
+ */
+typedef struct rtree_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *p, void *stream, void *ctx);
+    void *ctx;
+} rtree_allocator_t;
+
+/*
  * rtree_build -- bulk-load an R-tree with Sort-Tile-Recursive packing.
  *
  * The paper indexes a main-memory R-tree whose node holds up to F entries
@@ -136,12 +164,18 @@ typedef struct rtree_info {
  * rects: n*4 floats, ids: n int32 (NULL -> ids 0..n-1); host or device.
  * n = 0 builds a valid empty tree.  n must be < 2^31.
  * The inputs are copied; the caller keeps ownership and may free them once
- * the call returns.  *out receives the tree (free with rtree_free).
+ * the call returns.  alloc: the tree's device-memory hook (NULL: the default
+ * pool).  *out receives the tree (free with rtree_free).  The call returns
+ * once the inputs have been checked on the device (one host read) and the
+ * packing is enqueued on `stream`; work enqueued on `stream` afterwards may
+ * use the tree.
  * Errors: RTREE_EINVAL for a NaN coordinate, xmin > xmax or ymin > ymax in
- * any row, an unsupported fanout/layout, or NULL out; RTREE_ENOMEM.
+ * any row, an unsupported fanout/layout, an allocator with a NULL function,
+ * or NULL out; RTREE_ENOMEM.
  */
 RTREE_API rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
-                         const rtree_config_t *cfg, void *stream, rtree_t **out);
+                                   const rtree_config_t *cfg, const rtree_allocator_t *alloc,
+                                   void *stream, rtree_t **out);
 
 /* Releases the tree's device memory.  NULL is ignored. */
 RTREE_API void rtree_free(rtree_t *tree);
@@ -191,8 +225,17 @@ RTREE_API rtree_status rtree_export(const rtree_t *tree, int64_t *level_nodes, i
  * query.
  *
  * *out receives the result (free with rtree_result_free), resident on the
- * tree's device.  Errors: RTREE_EINVAL (NULL tree/out, q < 0), RTREE_ENOMEM,
- * RTREE_EINTERNAL, RTREE_ECUDA.
+ * tree's device, its buffers from the tree's allocator.  Stream order: the
+ * call reads two small values on the host (the sizes of the traversal's
+ * outputs, then the result's total) and returns while the last pass and the
+ * per-query sort still run on `stream`; rtree_result_total is valid on
+ * return, the offsets and ids once `stream` has reached the end of the call
+ * (rtree_result_wait, rtree_result_copy_to_host, or a stream
+ * synchronization).  Errors found on the device after the return (internal
+ * consistency checks, a work-queue wait that ran out) are reported by
+ * rtree_result_wait and rtree_result_copy_to_host.
+ * Errors: RTREE_EINVAL (NULL tree/out, q < 0), RTREE_ENOMEM,
+ * RTREE_EINTERNAL, RTREE_ETIMEOUT, RTREE_ECUDA.
  */
 RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *queries, int64_t q,
                                 const rtree_select_opts_t *opts, void *stream,
@@ -220,6 +263,8 @@ RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *quer
  * RTREE_EOVERFLOW with *total set to the size needed and incomplete outputs.
  * The first run of each bucket records its graph (it must not itself be
  * inside a stream capture).  A plan is used by one host thread at a time.
+ * The plan's buffers come from the tree's allocator; scratch that the
+ * recorded pipeline allocates is graph memory, owned by the graphs.
  */
 typedef struct rtree_plan rtree_plan_t;
 RTREE_API rtree_status rtree_plan_create(const rtree_t *tree, int64_t max_queries, int64_t max_ids,
@@ -453,12 +498,28 @@ RTREE_API const int64_t *rtree_result_offsets(const rtree_result_t *res); /* q+1
 RTREE_API const int32_t *rtree_result_ids(const rtree_result_t *res);     /* total (select) or 2*total (join) */
 
 /* Copies a result to caller-owned host arrays (offsets may be NULL; sized as
- * the accessors above say). */
+ * the accessors above say), on `stream` after the work that produced the
+ * result (whichever stream that ran on), and returns once the copies are
+ * done, with the device-side status of that work (see rtree_result_wait). */
 RTREE_API rtree_status rtree_result_copy_to_host(const rtree_result_t *res, int64_t *offsets,
                                        int32_t *ids, void *stream);
 
-/* Releases a result.  NULL is ignored. */
+/* Waits until the device work that produces the result has finished and
+ * returns its status: RTREE_OK, RTREE_EINTERNAL if a device-side consistency
+ * check failed, RTREE_ETIMEOUT if a bounded work-queue wait ran out (the
+ * result is then incomplete).  Results of calls that return only after their
+ * work has finished (rtree_join) return RTREE_OK at once. */
+RTREE_API rtree_status rtree_result_wait(const rtree_result_t *res);
+
+/* Releases a result (after the whole device has finished; the buffers go
+ * back to the allocator they came from).  NULL is ignored. */
 RTREE_API void rtree_result_free(rtree_result_t *res);
+
+/* Releases a result in the order of `stream`: work already enqueued on that
+ * stream (the producing call's, if it ran there) may still read it; work on
+ * other streams is not waited for.  The handle is invalid on return.  NULL
+ * is ignored. */
+RTREE_API void rtree_result_free_async(rtree_result_t *res, void *stream);
 
 /* Description of the last failure on this host thread ("" if none). */
 RTREE_API const char *rtree_last_error(void);

@@ -46,7 +46,7 @@ extern "C" rtree_status rtree_autotune(const float *rects, const int32_t *ids, i
             rtree_t *tree = nullptr;
             float build_ms = 0.f;
             cudaEventRecord(e0, s);
-            st = rtree_build(rects, ids, n, &cfg, stream, &tree);
+            st = rtree_build(rects, ids, n, &cfg, nullptr, stream, &tree);
             cudaEventRecord(e1, s);
             if (st != RTREE_OK)
                 break;

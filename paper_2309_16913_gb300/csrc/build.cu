@@ -404,16 +404,33 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     if (n == 0)
         return RTREE_OK;
 
-    // NaN and inverted rectangles are looked for first; the outcome is read
-    // with the root box at the end (the build's control flow does not depend
-    // on the coordinates, and an invalid input only wastes the build).
-    DevBuf<unsigned long long> bad(s);
-    RT_TRY(bad.alloc(1, "validation flag"));
-    RT_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
+    // NaN and inverted rectangles are looked for first, and the outcome is
+    // read at once through a mailbox (no copy-engine queue to wait behind):
+    // it is the one host read of the build, so that the rest of the packing
+    // runs in the order of `s` after the call has returned.
     {
-        KernelTimer kt_("validate", s);
-        k_validate<<<blocks_for(n), kThreads, 0, s>>>(rects, n, bad.p);
-        RT_LAUNCH();
+        DevBuf<unsigned long long> bad(s);
+        RT_TRY(bad.alloc(1, "validation flag"));
+        RT_CUDA(cudaMemsetAsync(bad.p, 0xff, sizeof(unsigned long long), s));
+        {
+            KernelTimer kt_("validate", s);
+            k_validate<<<blocks_for(n), kThreads, 0, s>>>(rects, n, bad.p);
+            RT_LAUNCH();
+        }
+        MailboxRef mb;
+        RT_TRY(mailbox_get(&mb.m));
+        PostList pl{};
+        pl.src[0] = bad.p;
+        pl.words[0] = 2;
+        pl.at[0] = 0;
+        pl.n = 1;
+        RT_TRY(mailbox_post(mb.m, pl, s));
+        RT_TRY(mailbox_wait(mb.m));
+        const volatile uint32_t *w = mb.m.h;
+        const unsigned long long h = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
+        if (h != ~0ull)
+            return fail(RTREE_EINVAL,
+                        "rectangle %llu has a NaN coordinate or xmin > xmax or ymin > ymax", h);
     }
 
     // ---- bottom-up packing
@@ -599,29 +616,28 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
                 k_ranges_up<<<blocks_for(P), kThreads, 0, s>>>(meta.p, t->level_base[e], P);
             RT_LAUNCH();
         }
-        // the validation outcome and the root box reach the host through a
-        // mailbox (no copy-engine queue to wait behind)
-        MailboxRef mb;
-        RT_TRY(mailbox_get(&mb.m));
-        PostList pl{};
-        pl.src[0] = bad.p;
-        pl.words[0] = 2;
-        pl.at[0] = 0;
-        pl.src[1] = boxes[H - 1]->p;
-        pl.words[1] = 4;
-        pl.at[1] = 2;
-        pl.n = 2;
-        RT_TRY(mailbox_post(mb.m, pl, s));
-        RT_TRY(mailbox_wait(mb.m));
-        const volatile uint32_t *w = mb.m.h;
-        const unsigned long long h = (unsigned long long)w[0] | ((unsigned long long)w[1] << 32);
-        if (h != ~0ull)
-            return fail(RTREE_EINVAL,
-                        "rectangle %llu has a NaN coordinate or xmin > xmax or ymin > ymax", h);
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t v = w[2 + c];
-            memcpy(&t->root_mbr[c], &v, 4);
+        // the root box goes to a mailbox of the tree, read when first asked
+        // for (tree_root_box): the call does not wait for the packing
+        Mailbox *mb = new Mailbox();
+        rtree_status st = mailbox_get(mb);
+        if (st != RTREE_OK) {
+            delete mb;
+            return st;
         }
+        PostList pl{};
+        pl.src[0] = boxes[H - 1]->p;
+        pl.words[0] = 4;
+        pl.at[0] = 0;
+        pl.n = 1;
+        st = mailbox_post(*mb, pl, s);
+        if (st != RTREE_OK) {
+            cudaEventSynchronize(mb->ev);
+            mailbox_put(mb);
+            delete mb;
+            return st;
+        }
+        t->root_mb = mb;
+        t->root_ready = false;
     }
     t->mbr = mbr.release();
     t->meta = meta.release();

@@ -17,6 +17,7 @@ namespace rt {
 
 static thread_local std::string g_err;
 static std::atomic<long long> g_alloc_countdown{-1};  // < 0: no injected failure
+thread_local const rtree_allocator_t *t_alloc = nullptr;
 
 rtree_status fail(rtree_status st, const char *fmt, ...)
 {
@@ -58,6 +59,12 @@ rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what)
             break;
         }
     }
+    if (t_alloc) {
+        *p = t_alloc->alloc(bytes, s, t_alloc->ctx);
+        if (!*p)
+            return fail(RTREE_ENOMEM, "the tree's allocator returned no memory: %zu bytes for %s", bytes, what);
+        return RTREE_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
@@ -74,9 +81,31 @@ rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what)
 
 void dfree(void *p, cudaStream_t s)
 {
-    if (p)
+    if (!p)
+        return;
+    if (t_alloc)
+        t_alloc->free(p, s, t_alloc->ctx);
+    else
         cudaFreeAsync(p, s);
 }
+
+namespace {
+// Gives p back to allocator a (null: the default pool): in the order of
+// stream s if `ordered`, else once the whole device has finished.
+void release(void *p, const rtree_allocator_t *a, cudaStream_t s, bool ordered)
+{
+    if (!p)
+        return;
+    if (!ordered)
+        cudaDeviceSynchronize();
+    if (a)
+        a->free(p, ordered ? s : nullptr, a->ctx);
+    else if (ordered)
+        cudaFreeAsync(p, s);
+    else
+        cudaFree(p);
+}
+}  // namespace
 
 int sm_count()
 {
@@ -128,23 +157,73 @@ rtree_status stage(const void *p, size_t bytes, size_t align, cudaStream_t s, De
 
 }  // namespace
 
-void free_tree_arrays(rtree *t)
+void free_tree_arrays(rtree *t, cudaStream_t s, bool ordered)
 {
-    if (t->mbr)
-        cudaFree(t->mbr);
-    if (t->meta)
-        cudaFree(t->meta);
-    if (t->nbox)
-        cudaFree(t->nbox);
-    if (t->ids)
-        cudaFree(t->ids);
+    const rtree_allocator_t *a = t->allocator();
+    release(t->mbr, a, s, ordered);
+    release(t->meta, a, s, ordered);
+    release(t->nbox, a, s, ordered);
+    release(t->ids, a, s, ordered);
     t->mbr = nullptr;
     t->meta = nullptr;
     t->nbox = nullptr;
     t->ids = nullptr;
+    if (t->root_mb) {  // a kernel may still write it: reused only after its event
+        mailbox_put_deferred(t->root_mb);
+        delete t->root_mb;
+        t->root_mb = nullptr;
+    }
+}
+
+void free_result_arrays(rtree_result *r, cudaStream_t s, bool ordered)
+{
+    const rtree_allocator_t *a = r->custom_alloc ? &r->alloc : nullptr;
+    release(r->offsets, a, s, ordered);
+    release(r->ids, a, s, ordered);
+    r->offsets = nullptr;
+    r->ids = nullptr;
+    if (r->status) {
+        mailbox_put_deferred(r->status);
+        delete r->status;
+        r->status = nullptr;
+    }
 }
 
 bool fanout_ok(int f) { return f == 4 || f == 8 || f == 16 || f == 32 || f == 64 || f == 128; }
+
+namespace {
+std::mutex g_root_mu;  // guards rtree::root_mb / root_ready of every tree
+}
+
+rtree_status tree_ready_on(const rtree *t, cudaStream_t s)
+{
+    if (!t)
+        return RTREE_OK;
+    std::lock_guard<std::mutex> g(g_root_mu);
+    if (t->root_mb)  // the build's last kernel records this event
+        RT_CUDA(cudaStreamWaitEvent(s, t->root_mb->ev, 0));
+    return RTREE_OK;
+}
+
+rtree_status tree_root_box(const rtree *t, float box[4])
+{
+    std::lock_guard<std::mutex> g(g_root_mu);
+    rtree *m = const_cast<rtree *>(t);
+    if (!m->root_ready && m->root_mb) {
+        RT_TRY(mailbox_wait(*m->root_mb));  // the build's packing has finished
+        const volatile uint32_t *w = m->root_mb->h;
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t v = w[c];
+            memcpy(&m->root_mbr[c], &v, 4);
+        }
+        mailbox_put(m->root_mb);
+        delete m->root_mb;
+        m->root_mb = nullptr;
+        m->root_ready = true;
+    }
+    memcpy(box, m->root_mbr, 4 * sizeof(float));
+    return RTREE_OK;
+}
 
 }  // namespace rt
 
@@ -160,7 +239,8 @@ const char *rtree_version(void) { return "rtree-gb300 0.1 (sm_103a)"; }
 void rtree_debug_fail_alloc_after(long long k) { g_alloc_countdown.store(k); }
 
 rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
-                         const rtree_config_t *cfg, void *stream, rtree_t **out)
+                         const rtree_config_t *cfg, const rtree_allocator_t *alloc, void *stream,
+                         rtree_t **out)
 {
     clear_error();
     if (!out)
@@ -179,6 +259,8 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
         return fail(RTREE_EINVAL, "rtree_build: fanout %d not in {4,8,16,32,64,128}", F);
     if (layout != RTREE_LAYOUT_SOA && layout != RTREE_LAYOUT_AOS && layout != RTREE_LAYOUT_LOHI)
         return fail(RTREE_EINVAL, "rtree_build: unknown layout %d", layout);
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(RTREE_EINVAL, "rtree_build: allocator with a NULL alloc or free function");
     try {
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         int dev = 0;
@@ -189,6 +271,11 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
         setup_device_pool(dev);
         rtree *t = new rtree();
         t->device = dev;
+        if (alloc) {
+            t->alloc = *alloc;
+            t->custom_alloc = true;
+        }
+        AllocScope scope(t->allocator());
         rtree_status st;
         {
             DevBuf<float4> rtmp(s);
@@ -200,8 +287,8 @@ rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
                 st = stage<int32_t>(ids, (size_t)n * 4, 4, s, itmp, &dids);
             if (st == RTREE_OK)
                 st = build_tree(drects, dids, n, F, layout, sort_children, s, t);
-            if (st == RTREE_OK) {
-                cudaError_t e = cudaStreamSynchronize(s);
+            if (st == RTREE_OK) {  // launch errors only: the packing runs on in the order of s
+                cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess)
                     st = fail(RTREE_ECUDA, "rtree_build: %s", cudaGetErrorString(e));
             }
@@ -235,11 +322,9 @@ void rtree_free_async(rtree_t *t, void *stream)
     if (!t)
         return;
     DeviceGuard guard(t->device);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    dfree(t->mbr, s);
-    dfree(t->meta, s);
-    dfree(t->nbox, s);
-    dfree(t->ids, s);
+    if (tree_ready_on(t, static_cast<cudaStream_t>(stream)) != RTREE_OK)
+        cudaDeviceSynchronize();  // could not order the release after the build: wait for it
+    free_tree_arrays(t, static_cast<cudaStream_t>(stream), true);
     delete t;
 }
 
@@ -255,7 +340,10 @@ rtree_status rtree_get_info(const rtree_t *t, rtree_info_t *info)
     info->layout = t->layout;
     info->device = t->device;
     info->device_bytes = t->bytes;
-    memcpy(info->root_mbr, t->root_mbr, sizeof(info->root_mbr));
+    {
+        DeviceGuard guard(t->device);
+        RT_TRY(tree_root_box(t, info->root_mbr));
+    }
     info->sort_children = t->sorted;
     memset(info->reserved, 0, sizeof(info->reserved));
     return RTREE_OK;
@@ -274,6 +362,7 @@ rtree_status rtree_export(const rtree_t *t, int64_t *level_nodes, int32_t *count
     try {
         DeviceGuard guard(t->device);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        RT_TRY(tree_ready_on(t, s));
         const int F = t->fanout;
         const int64_t M = t->nodes;
         for (int e = 0; e < t->levels; ++e)
@@ -347,27 +436,28 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
         return fail(RTREE_EINVAL, "rtree_range_select: unknown order %d", order);
     try {
         DeviceGuard guard(t->device);
+        AllocScope scope(t->allocator());
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         rtree_result *res = new rtree_result();
         res->device = t->device;
-        rtree_status st;
-        {
+        res->alloc = t->alloc;
+        res->custom_alloc = t->custom_alloc;
+        res->stream = stream;
+        rtree_status st = tree_ready_on(t, s);
+        if (st == RTREE_OK) {
             DevBuf<float4> qtmp(s);
             const float4 *dq = nullptr;
             st = stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq);
             if (st == RTREE_OK)
                 st = range_select(t, dq, q, sorted, mapping, order, s, res);
-            if (st == RTREE_OK) {
-                cudaError_t e = cudaStreamSynchronize(s);
+            if (st == RTREE_OK) {  // launch errors; the rest is reported by rtree_result_wait
+                cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess)
                     st = fail(RTREE_ECUDA, "rtree_range_select: %s", cudaGetErrorString(e));
             }
         }
         if (st != RTREE_OK) {
-            if (res->offsets)
-                cudaFree(res->offsets);
-            if (res->ids)
-                cudaFree(res->ids);
+            free_result_arrays(res);
             delete res;
             return st;
         }
@@ -377,6 +467,26 @@ rtree_status rtree_range_select(const rtree_t *t, const float *queries, int64_t 
     } catch (...) {
         return fail(RTREE_ENOMEM, "rtree_range_select: host allocation failed");
     }
+}
+
+rtree_status rtree_result_wait(const rtree_result_t *r)
+{
+    clear_error();
+    if (!r)
+        return fail(RTREE_EINVAL, "rtree_result_wait: result is NULL");
+    if (!r->status)
+        return RTREE_OK;
+    DeviceGuard guard(r->device);
+    RT_TRY(mailbox_wait(*r->status));
+    const volatile uint32_t *w = r->status->h;
+    const uint32_t sel = w[0], sort = w[1];
+    if (sel & 4u)
+        return fail(RTREE_ETIMEOUT, "range select: a work-queue wait exceeded its limit");
+    if (sel)
+        return fail(RTREE_EINTERNAL, "range select pass reported device flags 0x%x", sel);
+    if (sort)
+        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", sort);
+    return RTREE_OK;
 }
 
 namespace {
@@ -401,7 +511,9 @@ rtree_status select_host_call(const char *name, const rtree_t *t, const float *q
         return fail(RTREE_EINVAL, "%s: unknown order %d", name, order);
     try {
         DeviceGuard guard(t->device);
+        AllocScope scope(t->allocator());
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        RT_TRY(tree_ready_on(t, s));
         DevBuf<float4> qtmp(s);
         const float4 *dq = nullptr;
         RT_TRY(stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq));
@@ -467,7 +579,9 @@ rtree_status rtree_range_select_stats(const rtree_t *t, const float *queries, in
         return fail(RTREE_EINVAL, "rtree_range_select_stats: bad argument");
     try {
         DeviceGuard guard(t->device);
+        AllocScope scope(t->allocator());
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        RT_TRY(tree_ready_on(t, s));
         DevBuf<float4> qtmp(s);
         const float4 *dq = nullptr;
         RT_TRY(stage<float4>(queries, (size_t)q * 16, 16, s, qtmp, &dq));
@@ -529,18 +643,25 @@ rtree_status join_impl(const rtree_t *r, const rtree_t *s_tree, const rtree_join
         return fail(RTREE_EINVAL, "rtree_join: pruning needs both trees built with sort_children");
     try {
         DeviceGuard guard(r->device);
+        AllocScope scope(r->allocator());
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         rtree_result *res = new rtree_result();
         res->device = r->device;
-        rtree_status st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res, stats);
+        res->alloc = r->alloc;
+        res->custom_alloc = r->custom_alloc;
+        res->stream = stream;
+        rtree_status st = tree_ready_on(r, s);
+        if (st == RTREE_OK)
+            st = tree_ready_on(s_tree, s);
+        if (st == RTREE_OK)
+            st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res, stats);
         if (st == RTREE_OK) {
             cudaError_t e = cudaStreamSynchronize(s);
             if (e != cudaSuccess)
                 st = fail(RTREE_ECUDA, "rtree_join: %s", cudaGetErrorString(e));
         }
         if (st != RTREE_OK) {
-            if (res->ids)
-                cudaFree(res->ids);
+            free_result_arrays(res);
             delete res;
             return st;
         }
@@ -566,6 +687,8 @@ rtree_status rtree_result_copy_to_host(const rtree_result_t *r, int64_t *offsets
         return fail(RTREE_EINVAL, "rtree_result_copy_to_host: result is NULL");
     DeviceGuard guard(r->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (r->status)  // after the producing call's work, whichever stream it ran on
+        RT_CUDA(cudaStreamWaitEvent(s, r->status->ev, 0));
     if (offsets && r->offsets)
         RT_CUDA(cudaMemcpyAsync(offsets, r->offsets, (r->rows + 1) * sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, s));
@@ -573,7 +696,7 @@ rtree_status rtree_result_copy_to_host(const rtree_result_t *r, int64_t *offsets
     if (ids && nids > 0)
         RT_CUDA(cudaMemcpyAsync(ids, r->ids, nids * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RT_CUDA(cudaStreamSynchronize(s));
-    return RTREE_OK;
+    return rtree_result_wait(r);
 }
 
 void rtree_result_free(rtree_result_t *r)
@@ -581,10 +704,16 @@ void rtree_result_free(rtree_result_t *r)
     if (!r)
         return;
     DeviceGuard guard(r->device);
-    if (r->offsets)
-        cudaFree(r->offsets);
-    if (r->ids)
-        cudaFree(r->ids);
+    free_result_arrays(r);
+    delete r;
+}
+
+void rtree_result_free_async(rtree_result_t *r, void *stream)
+{
+    if (!r)
+        return;
+    DeviceGuard guard(r->device);
+    free_result_arrays(r, static_cast<cudaStream_t>(stream), true);
     delete r;
 }
 

@@ -34,14 +34,34 @@ void clear_error();
     } while (0)
 
 // ------------------------------------------------------------------ memory
-// Device memory from the stream-ordered pool of the current device.  A
-// host-side counter can make the k-th allocation fail (fault injection for
-// tests; no GPU fault is involved).
+// The device-memory hook of the call in progress on this host thread (the
+// tree's allocator), or null for the stream-ordered pool of the current
+// device (cudaMallocAsync / cudaFreeAsync).  Entry points set it for their
+// duration with an AllocScope.
+extern thread_local const rtree_allocator_t *t_alloc;
+struct AllocScope {
+    const rtree_allocator_t *prev;
+    explicit AllocScope(const rtree_allocator_t *a) : prev(t_alloc) { t_alloc = a; }
+    ~AllocScope() { t_alloc = prev; }
+    AllocScope(const AllocScope &) = delete;
+    AllocScope &operator=(const AllocScope &) = delete;
+};
+// Device memory from t_alloc, usable in the order of stream s.  A host-side
+// counter can make the k-th allocation fail (fault injection for tests; no
+// GPU fault is involved).
 rtree_status dmalloc(void **p, size_t bytes, cudaStream_t s, const char *what);
 // Keeps freed blocks in the device's default pool between calls (once per device).
 void setup_device_pool(int dev);
-// Releases a tree's device arrays (not the struct).
-void free_tree_arrays(rtree *t);
+// Releases a tree's device arrays (not the struct): after the whole device
+// has finished when s is null, else in the order of stream s.
+void free_tree_arrays(rtree *t, cudaStream_t s = nullptr, bool ordered = false);
+// The tree's bounding box, waiting (once) for the build that posted it.
+rtree_status tree_root_box(const rtree *t, float box[4]);
+// Orders stream s after the tree's build (the build returns before its
+// packing has run; a call on another stream must not read the tree early).
+rtree_status tree_ready_on(const rtree *t, cudaStream_t s);
+// Releases a result's device arrays the same way.
+void free_result_arrays(rtree_result *r, cudaStream_t s = nullptr, bool ordered = false);
 bool fanout_ok(int f);
 
 // Makes `dev` current for the scope, restoring the previous device after.
@@ -142,6 +162,8 @@ void timing_add_replay(const char *name, long long launches);
 //         [elo, ehi) = the ids of all entries under the node.
 //   nbox: per node, its bounding box (equal to its entry in the parent).
 //   ids : entry ids, leaves in node order, entries in slot order.
+struct Mailbox;
+
 struct TreeDev {
     const float *mbr;
     const int4 *meta;
@@ -159,6 +181,8 @@ struct TreeDev {
 
 struct rtree {
     int device = 0;
+    rtree_allocator_t alloc{};  // the device-memory hook (custom_alloc), else the default pool
+    bool custom_alloc = false;
     int32_t fanout = 16;
     int32_t layout = RTREE_LAYOUT_SOA;
     int32_t sorted = 0;  // built with sort_children
@@ -171,8 +195,12 @@ struct rtree {
     int4 *meta = nullptr;
     float4 *nbox = nullptr;
     int32_t *ids = nullptr;
-    float root_mbr[4] = {0, 0, 0, 0};
+    float root_mbr[4] = {0, 0, 0, 0};  // valid once root_ready (see tree_root_box)
+    bool root_ready = true;
+    rt::Mailbox *root_mb = nullptr;     // the build's posted root box until it is read
     int64_t bytes = 0;
+
+    const rtree_allocator_t *allocator() const { return custom_alloc ? &alloc : nullptr; }
 
     rt::TreeDev view() const
     {
@@ -197,6 +225,10 @@ struct rtree_result {
     int64_t total = 0;  // ids (select) or pairs (join)
     int64_t *offsets = nullptr;
     int32_t *ids = nullptr;
+    rtree_allocator_t alloc{};  // where offsets and ids came from (custom_alloc)
+    bool custom_alloc = false;
+    void *stream = nullptr;     // the stream the result was produced on
+    rt::Mailbox *status = nullptr;  // device flags of work still in flight, posted at its end
 };
 
 namespace rt {
@@ -379,6 +411,9 @@ struct PostList {
 rtree_status post_words(const PostList &l, uint32_t *dst, cudaStream_t s);
 rtree_status mailbox_get(Mailbox *m);
 void mailbox_put(Mailbox *m);
+// Hands m back while a kernel may still post into it: it is reused only
+// after its event has completed.
+void mailbox_put_deferred(Mailbox *m);
 // Enqueues the copy kernel on s, then records m.ev on s.
 rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s);
 rtree_status mailbox_wait(const Mailbox &m);
@@ -437,6 +472,8 @@ rtree_status tree_join(const rtree *r, const rtree *s_tree, bool prune, cudaStre
 // read, freed on `cs` when the call is finished.
 struct rtree_pending {
     int device = 0;
+    rtree_allocator_t alloc{};  // the tree's device-memory hook (custom_alloc)
+    bool custom_alloc = false;
     cudaStream_t cs = nullptr;
     cudaEvent_t ev[33] = {};
     rt::Mailbox flags;  // the device flags, posted behind the last chunk

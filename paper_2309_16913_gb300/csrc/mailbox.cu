@@ -20,6 +20,7 @@ namespace {
 
 std::mutex g_mu;
 std::vector<Mailbox> g_free[64];
+std::vector<Mailbox> g_deferred[64];  // handed back while a post into them may still be pending
 
 __global__ void k_post(PostList l, uint32_t *__restrict__ dst)
 {
@@ -41,6 +42,16 @@ rtree_status mailbox_get(Mailbox *m)
         return fail(RTREE_EINVAL, "device %d out of range", dev);
     {
         std::lock_guard<std::mutex> g(g_mu);
+        for (size_t i = 0; i < g_deferred[dev].size();) {  // reclaim those whose post has run
+            if (cudaEventQuery(g_deferred[dev][i].ev) == cudaSuccess) {
+                g_free[dev].push_back(g_deferred[dev][i]);
+                g_deferred[dev][i] = g_deferred[dev].back();
+                g_deferred[dev].pop_back();
+            } else {
+                cudaGetLastError();  // cudaErrorNotReady
+                ++i;
+            }
+        }
         if (!g_free[dev].empty()) {
             *m = g_free[dev].back();
             g_free[dev].pop_back();
@@ -71,6 +82,15 @@ void mailbox_put(Mailbox *m)
         return;
     std::lock_guard<std::mutex> g(g_mu);
     g_free[m->device].push_back(*m);
+    *m = Mailbox{};
+}
+
+void mailbox_put_deferred(Mailbox *m)
+{
+    if (!m->h)
+        return;
+    std::lock_guard<std::mutex> g(g_mu);
+    g_deferred[m->device].push_back(*m);
     *m = Mailbox{};
 }
 

@@ -161,6 +161,7 @@ extern "C" rtree_status rtree_range_select_noalloc(const rtree_t *t, const float
                                   "offsets 8-byte aligned, ids 4-byte aligned");
     CurrentDevice guard(t->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RT_TRY(tree_ready_on(t, s));
     unsigned char *scratch = nullptr;
     RT_TRY(scratch_address(t->device, &scratch));
     int32_t *counts = reinterpret_cast<int32_t *>(scratch);

@@ -56,9 +56,10 @@ __device__ __forceinline__ uint32_t cell_of(float c, float lo, float w)
     return v < (1u << kGridBits) ? v : (1u << kGridBits) - 1u;
 }
 
-__global__ void k_hilbert_keys(const float4 *__restrict__ q, int64_t Q, float4 box,
+__global__ void k_hilbert_keys(const float4 *__restrict__ q, int64_t Q, const float4 *__restrict__ root,
                                uint32_t *__restrict__ keys, uint32_t *__restrict__ idx)
 {
+    const float4 box = *root;
     const float wx = box.z - box.x, wy = box.w - box.y;
     const bool okx = wx > 0.f && wx < __int_as_float(0x7f800000);
     const bool oky = wy > 0.f && wy < __int_as_float(0x7f800000);
@@ -84,11 +85,10 @@ rtree_status hilbert_order(const rtree *t, const float4 *queries, int64_t Q, uin
     RT_TRY(k0.alloc(Q, "query order keys"));
     RT_TRY(v0.alloc(Q, "query order"));
     RT_TRY(k1.alloc(Q, "query order keys"));
-    const float4 box = make_float4(t->root_mbr[0], t->root_mbr[1], t->root_mbr[2], t->root_mbr[3]);
-    {
+    {  // the tree's bounding box is read on the device: the root's node box
         KernelTimer kt_("hilbert_keys", s);
         int64_t b = (Q + 255) / 256;
-        k_hilbert_keys<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(queries, Q, box, k0.p, v0.p);
+        k_hilbert_keys<<<(unsigned)(b > 65536 ? 65536 : b), 256, 0, s>>>(queries, Q, t->nbox, k0.p, v0.p);
         RT_LAUNCH();
     }
     return radix_sort_pairs(k0.p, v0.p, k1.p, order, Q, 0, 32, s);

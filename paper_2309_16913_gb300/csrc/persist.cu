@@ -275,7 +275,7 @@ rtree_status save_impl(const rtree *t, const char *path, cudaStream_t s)
     h.levels = t->levels;
     h.n = t->n;
     h.nodes = t->nodes;
-    memcpy(h.root_mbr, t->root_mbr, sizeof(h.root_mbr));
+    RT_TRY(tree_root_box(t, h.root_mbr));
     for (int e = 0; e < t->levels; ++e)
         h.level_nodes[e] = t->level_nodes[e];
     size_t sec[4];

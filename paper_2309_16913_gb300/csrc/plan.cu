@@ -66,8 +66,15 @@ void free_plan(rtree_plan *p)
     for (Graph &g : p->graphs)
         cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
-    if (p->block)
-        cudaFree(p->block);
+    if (p->block) {
+        const rtree_allocator_t *a = p->tree ? p->tree->allocator() : nullptr;
+        if (a) {
+            cudaDeviceSynchronize();
+            a->free(p->block, nullptr, a->ctx);
+        } else {
+            cudaFree(p->block);
+        }
+    }
     if (p->host)
         cudaFreeHost(p->host);
     if (p->cap_stream)
@@ -105,7 +112,14 @@ rtree_status allocate(rtree_plan *p)
     size_t total = 0;
     for (const Piece &pc : pieces)
         total += (pc.bytes + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc(&p->block, total);
+    if (const rtree_allocator_t *a = p->tree->allocator()) {  // the tree's device-memory hook
+        p->block = a->alloc(total, nullptr, a->ctx);
+        if (!p->block)
+            return fail(RTREE_ENOMEM, "rtree_plan_create: the tree's allocator returned no memory (%zu bytes)",
+                        total);
+        RT_CUDA(cudaDeviceSynchronize());  // usable by the plan's own streams
+    }
+    cudaError_t e = p->block ? cudaSuccess : cudaMalloc(&p->block, total);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
         return fail(RTREE_ENOMEM, "rtree_plan_create: %zu bytes of device memory not available", total);
@@ -129,6 +143,10 @@ rtree_status allocate(rtree_plan *p)
 rtree_status capture(rtree_plan *p, int64_t qb, Graph *out)
 {
     cudaStream_t s = p->cap_stream;
+    // scratch allocated while capturing becomes graph memory (cudaMallocAsync
+    // inside a capture), owned by the graph: never the tree's allocator, whose
+    // blocks would be handed out again while the graph still uses them
+    AllocScope scope(nullptr);
     RT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     timing_capture_begin();
     rtree_status st = select_enqueue(p->tree, p->queries, qb, p->mapping, p->b, s);
@@ -254,6 +272,7 @@ rtree_status rtree_plan_run(rtree_plan_t *p, const float *queries, int64_t q, vo
     try {
         CurrentDevice guard(p->device);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        RT_TRY(tree_ready_on(p->tree, s));
         const int64_t qb = bucket_of(q > 0 ? q : 1, p->max_q);
         if (q > 0)
             RT_CUDA(cudaMemcpyAsync(p->queries, queries, q * sizeof(float4),

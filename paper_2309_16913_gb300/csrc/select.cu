@@ -680,12 +680,53 @@ SelIO unlimited()
     return io;
 }
 
+// Reads n <= 8 device words of the listed sources on the host: one kernel
+// stores them into a mailbox, the host waits for its event (never behind
+// copies other calls queued on a copy engine).
+rtree_status read_words(const PostList &l, cudaStream_t s, uint32_t *out, int nwords)
+{
+    MailboxRef mb;
+    RT_TRY(mailbox_get(&mb.m));
+    RT_TRY(mailbox_post(mb.m, l, s));
+    RT_TRY(mailbox_wait(mb.m));
+    for (int i = 0; i < nwords; ++i)
+        out[i] = ((const volatile uint32_t *)mb.m.h)[i];
+    return RTREE_OK;
+}
+
+int64_t word64(const uint32_t *w) { return (int64_t)((uint64_t)w[0] | ((uint64_t)w[1] << 32)); }
+
+// Posts the select and sort flags (2 words) to the result's status mailbox
+// behind the call's last kernel; rtree_result_wait reads them.
+rtree_status post_status(const int32_t *flags, cudaStream_t s, rtree_result *res)
+{
+    Mailbox *mb = new Mailbox();
+    rtree_status st = mailbox_get(mb);
+    if (st != RTREE_OK) {
+        delete mb;
+        return st;
+    }
+    PostList pl{};
+    pl.src[0] = flags;
+    pl.words[0] = 2;
+    pl.at[0] = 0;
+    pl.n = 1;
+    st = mailbox_post(*mb, pl, s);
+    if (st != RTREE_OK) {
+        cudaEventSynchronize(mb->ev);
+        mailbox_put(mb);
+        delete mb;
+        return st;
+    }
+    res->status = mb;
+    return RTREE_OK;
+}
+
 rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree_result *res)
 {
     RT_CUDA(cudaMemsetAsync(off.p, 0, (Q + 1) * sizeof(int64_t), s));
     DevBuf<int32_t> ids(s);
     RT_TRY(ids.alloc(1, "select ids"));
-    RT_CUDA(cudaStreamSynchronize(s));
     res->offsets = off.release();
     res->ids = ids.release();
     return RTREE_OK;
@@ -725,12 +766,27 @@ rtree_status range_select_bounded(const rtree *t, const float4 *queries, int64_t
     RT_TRY(launch(PASS_BOUND, t, queries, Q, io, ctr.p, flags.p, s));
     RT_TRY(scan_exclusive(cnt_leaf.p, off_leaf.p, Q, s));
     RT_TRY(scan_exclusive(cnt_rng.p, off_rng.p, Q, s));
+    // host read 1 of 2: the sizes of the descriptor pass's outputs and the flags
     int64_t h[2] = {0, 0};
     int32_t hflags = 0;
-    RT_CUDA(cudaMemcpyAsync(&h[0], off_leaf.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaMemcpyAsync(&h[1], off_rng.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
+    {
+        PostList pl{};
+        pl.src[0] = off_leaf.p + Q;
+        pl.words[0] = 2;
+        pl.at[0] = 0;
+        pl.src[1] = off_rng.p + Q;
+        pl.words[1] = 2;
+        pl.at[1] = 2;
+        pl.src[2] = flags.p;
+        pl.words[2] = 1;
+        pl.at[2] = 4;
+        pl.n = 3;
+        uint32_t w[5];
+        RT_TRY(read_words(pl, s, w, 5));
+        h[0] = word64(w);
+        h[1] = word64(w + 2);
+        hflags = (int32_t)w[4];
+    }
     if (hflags)
         return fail(RTREE_EINTERNAL, "select bound pass reported device flags 0x%x", hflags);
 
@@ -748,9 +804,23 @@ rtree_status range_select_bounded(const rtree *t, const float4 *queries, int64_t
     so.counts_leaf = cnt_leaf.p;  // exact leaf hits (the bounds are scanned already)
     RT_TRY(launch(PASS_DESC, t, queries, Q, so, ctr.p + 1, flags.p, s));
     RT_TRY(scan_exclusive(cnt.p, off.p, Q, s));
+    // host read 2 of 2: the total (it sizes the result and is returned)
     int64_t total = 0;
-    RT_CUDA(cudaMemcpyAsync(&total, off.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
+    {
+        PostList pl{};
+        pl.src[0] = off.p + Q;
+        pl.words[0] = 2;
+        pl.at[0] = 0;
+        pl.src[1] = flags.p;
+        pl.words[1] = 1;
+        pl.at[1] = 2;
+        pl.n = 2;
+        uint32_t w[3];
+        RT_TRY(read_words(pl, s, w, 3));
+        total = word64(w);
+        if (w[2])
+            return fail(RTREE_EINTERNAL, "select descriptor pass reported device flags 0x%x", w[2]);
+    }
     DevBuf<int32_t> ids(s);
     RT_TRY(ids.alloc(total, "select ids"));
     SortSources src{};
@@ -761,13 +831,8 @@ rtree_status range_select_bounded(const rtree *t, const float4 *queries, int64_t
     src.off_rng = off_rng.p;
     src.tree_ids = t->ids;
     RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s, flags.p + 1));
-    int32_t hf2[2] = {0, 0};
-    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
-    if (hf2[1])
-        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
-    if (hf2[0])
-        return fail(RTREE_EINTERNAL, "select descriptor pass reported device flags 0x%x", hf2[0]);
+    // the sort runs on in the order of s; its flags reach the result's status
+    RT_TRY(post_status(flags.p, s, res));
     res->total = total;
     res->offsets = off.release();
     res->ids = ids.release();
@@ -830,15 +895,36 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         RT_TRY(scan_exclusive(cnt_leaf.p, off_leaf.p, Q, s));
         RT_TRY(scan_exclusive(cnt_rng.p, off_rng.p, Q, s));
     }
+    // the one host read: the total, the descriptor sizes and the flags
     int64_t h[3] = {0, 0, 0};
     int32_t hflags = 0;
-    RT_CUDA(cudaMemcpyAsync(&h[0], off.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (sorted) {
-        RT_CUDA(cudaMemcpyAsync(&h[1], off_leaf.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        RT_CUDA(cudaMemcpyAsync(&h[2], off_rng.p + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    {
+        PostList pl{};
+        pl.src[0] = off.p + Q;
+        pl.words[0] = 2;
+        pl.at[0] = 0;
+        pl.src[1] = flags.p;
+        pl.words[1] = 1;
+        pl.at[1] = 2;
+        pl.n = 2;
+        if (sorted) {
+            pl.src[2] = off_leaf.p + Q;
+            pl.words[2] = 2;
+            pl.at[2] = 3;
+            pl.src[3] = off_rng.p + Q;
+            pl.words[3] = 2;
+            pl.at[3] = 5;
+            pl.n = 4;
+        }
+        uint32_t w[7] = {};
+        RT_TRY(read_words(pl, s, w, sorted ? 7 : 3));
+        h[0] = word64(w);
+        hflags = (int32_t)w[2];
+        if (sorted) {
+            h[1] = word64(w + 3);
+            h[2] = word64(w + 5);
+        }
     }
-    RT_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
     if (hflags & FLAG_TIMEOUT)
         return fail(RTREE_ETIMEOUT, "select count pass: a work-queue wait exceeded its limit");
     if (hflags)
@@ -889,16 +975,9 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
         src.tree_ids = t->ids;
         RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s, flags.p + 1));
     }
-    int32_t hf2[2] = {0, 0};
-    RT_CUDA(cudaMemcpyAsync(hf2, flags.p, sizeof(hf2), cudaMemcpyDeviceToHost, s));
-    RT_CUDA(cudaStreamSynchronize(s));
-    if (hf2[1])
-        return fail(RTREE_EINTERNAL, "segmented sort reported device flags 0x%x", hf2[1]);
-    hflags = hf2[0];
-    if (hflags & FLAG_TIMEOUT)
-        return fail(RTREE_ETIMEOUT, "select second pass: a work-queue wait exceeded its limit");
-    if (hflags)
-        return fail(RTREE_EINTERNAL, "select scatter pass reported device flags 0x%x", hflags);
+    // the second pass (and sort) run on in the order of s; their flags reach
+    // the result's status
+    RT_TRY(post_status(flags.p, s, res));
     res->total = total;
     res->offsets = off.release();
     res->ids = ids.release();
@@ -1079,6 +1158,8 @@ rtree_status range_select_host_begin(const rtree *t, const float4 *queries, int6
     } pd;
     rtree_pending *p = pd.p;
     p->device = t->device;
+    p->alloc = t->alloc;
+    p->custom_alloc = t->custom_alloc;
     RT_CUDA(cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking));
     for (int k = 0; k <= kChunks; ++k)
         RT_CUDA(cudaEventCreateWithFlags(&p->ev[k], cudaEventDisableTiming));
@@ -1162,6 +1243,7 @@ rtree_status range_select_host_finish(rtree_pending *p)
         hf[1] = f[1];
     }
     if (p->cs) {
+        AllocScope scope(p->custom_alloc ? &p->alloc : nullptr);
         dfree(p->ids, p->cs);
         dfree(p->off, p->cs);
         cudaStreamDestroy(p->cs);

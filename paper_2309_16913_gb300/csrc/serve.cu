@@ -117,7 +117,7 @@ void run_batch(rtree_server *srv, rtree_plan_t *plan, cudaStream_t s, std::vecto
             r.offsets.resize(nq + 1);
             r.ids.resize(rtree_result_total(res));
             st = rtree_result_copy_to_host(res, r.offsets.data(), r.ids.empty() ? nullptr : r.ids.data(), s);
-            rtree_result_free(res);
+            rtree_result_free_async(res, s);
         }
         replies[0].status = st;
         return;
@@ -220,7 +220,7 @@ void worker_main(rtree_server *srv, int index)
                 replies[0].ids.resize(rtree_result_total(res));
                 rs = rtree_result_copy_to_host(res, replies[0].offsets.data(),
                                                replies[0].ids.empty() ? nullptr : replies[0].ids.data(), s);
-                rtree_result_free(res);
+                rtree_result_free_async(res, s);
             }
             replies[0].status = rs;
             fallbacks = 1;

@@ -4,7 +4,8 @@
 // always counted.  When timing is enabled, a pair of CUDA events is recorded
 // around the launch on the launching stream; elapsed times are resolved once
 // the stream has been synchronized (at the end of every C-ABI call, or when
-// the totals are read).
+// the totals are read).  Resolving at the end of a call only takes the pairs
+// whose work has finished; reading the totals waits for all of them.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -57,9 +58,23 @@ cudaEvent_t get_event()
     return e;
 }
 
-void resolve_locked()
+// Adds the times of the recorded pairs.  wait: every pair, waiting for its
+// events; else only pairs whose end event has completed (the others stay
+// pending), so that a call can resolve without waiting for its own work
+// still in flight.
+void resolve_locked(bool wait)
 {
-    for (const Pending &p : g_pending) {
+    size_t keep = 0;
+    for (size_t i = 0; i < g_pending.size(); ++i) {
+        const Pending p = g_pending[i];
+        if (!wait) {
+            const cudaError_t q = cudaEventQuery(p.b);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();
+                g_pending[keep++] = p;
+                continue;
+            }
+        }
         float ms = 0.f;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
             g_entries[p.entry].ms += ms;
@@ -68,7 +83,7 @@ void resolve_locked()
         g_pool.push_back(p.a);
         g_pool.push_back(p.b);
     }
-    g_pending.clear();
+    g_pending.resize(keep);
 }
 
 }  // namespace
@@ -148,7 +163,7 @@ PhaseTimer::~PhaseTimer()
 void timing_resolve()
 {
     std::lock_guard<std::mutex> g(g_mu);
-    resolve_locked();
+    resolve_locked(false);
 }
 
 }  // namespace rt
@@ -166,7 +181,7 @@ void rtree_timing_enable(int on)
 void rtree_timing_reset(void)
 {
     std::lock_guard<std::mutex> g(g_mu);
-    resolve_locked();
+    resolve_locked(true);
     for (Entry &e : g_entries) {
         e.launches = 0;
         e.ms = 0.0;
@@ -177,7 +192,7 @@ void rtree_timing_reset(void)
 int rtree_timing_get(int index, const char **name, long long *launches, double *ms)
 {
     std::lock_guard<std::mutex> g(g_mu);
-    resolve_locked();
+    resolve_locked(true);
     if (index < 0 || index >= (int)g_entries.size())
         return 0;
     if (name)

@@ -91,6 +91,74 @@ class rtree_info_t(C.Structure):
                 ("sort_children", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
+# device-memory hook (rtree_allocator_t): alloc(bytes, stream, ctx) -> pointer,
+# free(pointer, stream, ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class rtree_allocator_t(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class Allocator:
+    """A device-memory hook for rtree_build: every device buffer the library
+    allocates for the tree (the tree, the scratch of calls on it, their
+    results) comes from ``alloc(nbytes, stream) -> int`` (0 on failure) and
+    goes back through ``free(ptr, stream)``; ``stream`` is the raw
+    cudaStream_t of the call (0 = legacy default stream).  The callbacks run
+    on whichever host thread calls into the library, with the GIL taken.
+    Keep the object alive as long as the tree and its results (RTree and
+    Result objects hold a reference).  Counts calls and live bytes."""
+
+    def __init__(self, alloc, free):
+        self._alloc, self._free = alloc, free
+        self.allocs = self.frees = 0
+        self.live = {}
+
+        def c_alloc(nbytes, stream, _ctx):
+            try:
+                p = int(self._alloc(int(nbytes), int(stream or 0)) or 0)
+            except Exception:  # an exception must not cross into C
+                p = 0
+            if p:
+                self.allocs += 1
+                self.live[p] = int(nbytes)
+            return p
+
+        def c_free(ptr, stream, _ctx):
+            try:
+                if ptr:
+                    self.frees += 1
+                    self.live.pop(int(ptr), None)
+                    self._free(int(ptr), int(stream or 0))
+            except Exception:
+                pass
+
+        self._c_alloc, self._c_free = ALLOC_FN(c_alloc), FREE_FN(c_free)
+        self.struct = rtree_allocator_t(self._c_alloc, self._c_free, None)
+
+
+class TorchAllocator(Allocator):
+    """Takes the library's device memory from PyTorch's caching allocator
+    (torch.cuda.caching_allocator_alloc / caching_allocator_delete), on the
+    stream of each call, so the library shares one pool with the tensors
+    around it.  Each allocation is a call into Python: use the default pool
+    (no allocator) where many small calls run concurrently with busy Python
+    threads (e.g. a serving loop whose client spins on the GIL)."""
+
+    def __init__(self):
+        import torch
+
+        def alloc(nbytes, stream):
+            return torch.cuda.caching_allocator_alloc(max(1, nbytes), None, stream)
+
+        def free(ptr, _stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        super().__init__(alloc, free)
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -98,7 +166,7 @@ _lib = None
 def _bind(lib):
     vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
     sigs = {
-        "rtree_build": (C.c_int, [vp, vp, i64, C.POINTER(rtree_config_t), vp, C.POINTER(vp)]),
+        "rtree_build": (C.c_int, [vp, vp, i64, C.POINTER(rtree_config_t), vp, vp, C.POINTER(vp)]),
         "rtree_free": (None, [vp]),
         "rtree_free_async": (None, [vp, vp]),
         "rtree_get_info": (C.c_int, [vp, C.POINTER(rtree_info_t)]),
@@ -122,6 +190,8 @@ def _bind(lib):
         "rtree_result_ids": (vp, [vp]),
         "rtree_result_copy_to_host": (C.c_int, [vp, vp, vp, vp]),
         "rtree_result_free": (None, [vp]),
+        "rtree_result_free_async": (None, [vp, vp]),
+        "rtree_result_wait": (C.c_int, [vp]),
         "rtree_last_error": (C.c_char_p, []),
         "rtree_version": (C.c_char_p, []),
         "rtree_debug_fail_alloc_after": (None, [C.c_longlong]),
@@ -230,8 +300,10 @@ def _stream(stream) -> int:
 
 # ------------------------------------------------- C names, thin wrappers
 def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None,
-                sort_children: bool = False) -> int:
-    """Builds a tree; returns the opaque handle (free with rtree_free)."""
+                sort_children: bool = False, allocator: Allocator | None = None) -> int:
+    """Builds a tree; returns the opaque handle (free with rtree_free).
+    ``allocator`` (an :class:`Allocator`) supplies the tree's device memory;
+    None selects the library's default pool."""
     lib = load_library()
     rp, n, keep_r = _as_rows(rects, "rects")
     ip, keep_i = _as_ids(ids, n)
@@ -240,7 +312,8 @@ def rtree_build(rects, ids=None, fanout: int = 16, layout: str | int = "soa", st
     cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
     cfg.sort_children = 1 if sort_children else 0
     out = C.c_void_p()
-    _check(lib.rtree_build(rp, ip, n, C.byref(cfg), _stream(stream), C.byref(out)), lib)
+    ap = C.byref(allocator.struct) if allocator is not None else None
+    _check(lib.rtree_build(rp, ip, n, C.byref(cfg), ap, _stream(stream), C.byref(out)), lib)
     del keep_r, keep_i
     return out.value
 
@@ -475,6 +548,12 @@ def rtree_result_free(res: int) -> None:
         load_library().rtree_result_free(res)
 
 
+def rtree_result_wait(res: int) -> None:
+    """Waits for the work producing the result; raises on a device-side error."""
+    lib = load_library()
+    _check(lib.rtree_result_wait(res), lib)
+
+
 def rtree_last_error() -> str:
     return (load_library().rtree_last_error() or b"").decode()
 
@@ -636,18 +715,27 @@ class _DeviceArray:
 
 
 class Result:
-    """A select (CSR) or join (pairs) result resident on the device."""
+    """A select (CSR) or join (pairs) result resident on the device.  A select
+    returns while its last kernels still run on the call's stream: ``total``
+    is valid at once; the arrays once that stream has reached them
+    (``wait()``, ``to_numpy()``, or work and tensors on the same stream)."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, owner=None):
         self.handle = handle
+        self._owner = owner  # keeps the tree's allocator alive until the result is freed
 
     def __del__(self):
         self.close()
 
-    def close(self):
+    def close(self, stream=None):
+        """Frees the result; with ``stream`` in that stream's order
+        (rtree_result_free_async), without waiting for the device."""
         h, self.handle = getattr(self, "handle", None), None
         if h:
-            rtree_result_free(h)
+            if stream is None:
+                rtree_result_free(h)
+            else:
+                load_library().rtree_result_free_async(h, _stream(stream))
 
     @property
     def total(self) -> int:
@@ -661,6 +749,12 @@ class Result:
     def is_join(self) -> bool:
         return rtree_result_offsets(self.handle) == 0
 
+    def wait(self) -> "Result":
+        """Waits for the device work that produces this result (raises
+        RTreeError on a device-side error)."""
+        rtree_result_wait(self.handle)
+        return self
+
     def to_numpy(self, stream=None):
         """(offsets, ids) for select; (None, pairs[total, 2]) for join."""
         return rtree_result_copy_to_host(self.handle, stream)
@@ -668,12 +762,14 @@ class Result:
     def offsets_tensor(self):
         """Zero-copy torch view of the offsets (keeps this result alive)."""
         import torch
+        self.wait()
         ptr = rtree_result_offsets(self.handle)
         return torch.as_tensor(_DeviceArray(self, ptr, (self.rows + 1,), "<i8"), device="cuda")
 
     def ids_tensor(self):
         """Zero-copy torch view of the ids (select) or pairs (join)."""
         import torch
+        self.wait()
         ptr = rtree_result_ids(self.handle)
         shape = (self.total, 2) if self.is_join else (self.total,)
         if self.total == 0:
@@ -754,17 +850,20 @@ class RTree:
     """An R-tree on the GPU: build, range select, join."""
 
     def __init__(self, rects, ids=None, fanout: int = 16, layout: str | int = "soa", stream=None,
-                 sort_children: bool = False):
+                 sort_children: bool = False, allocator: Allocator | None = None):
         self.handle = None
-        self.handle = rtree_build(rects, ids, fanout, layout, stream, sort_children)
+        self.allocator = allocator
+        self.handle = rtree_build(rects, ids, fanout, layout, stream, sort_children, allocator)
 
     def __del__(self):
         self.close()
 
-    def close(self):
+    def close(self, stream=None):
+        """Frees the tree; with ``stream`` in that stream's order
+        (rtree_free_async), without waiting for the device."""
         h, self.handle = getattr(self, "handle", None), None
         if h:
-            rtree_free(h)
+            rtree_free(h, stream)
 
     def __enter__(self):
         return self
@@ -782,6 +881,7 @@ class RTree:
     def load(cls, path: str, device: int = -1, stream=None) -> "RTree":
         t = cls.__new__(cls)
         t.handle = None
+        t.allocator = None
         t.handle = rtree_load(path, device, stream)
         return t
 
@@ -790,15 +890,16 @@ class RTree:
 
     def range_select(self, queries, unsorted: bool = False, mapping="auto", stream=None,
                      order="input") -> Result:
-        return Result(rtree_range_select(self.handle, queries, unsorted, mapping, stream, order))
+        return Result(rtree_range_select(self.handle, queries, unsorted, mapping, stream, order),
+                      self.allocator)
 
     def select_stats(self, queries, stream=None) -> dict:
         return rtree_range_select_stats(self.handle, queries, stream)
 
     def join(self, other: "RTree", stream=None, prune: str | int | None = None) -> Result:
         if prune is None:
-            return Result(rtree_join(self.handle, other.handle, stream))
-        return Result(rtree_join_ex(self.handle, other.handle, prune, stream))
+            return Result(rtree_join(self.handle, other.handle, stream), self.allocator)
+        return Result(rtree_join_ex(self.handle, other.handle, prune, stream), self.allocator)
 
     def join_stats(self, other: "RTree", stream=None, prune: str | int = "auto") -> dict:
         return rtree_join_stats(self.handle, other.handle, prune, stream)

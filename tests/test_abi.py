@@ -61,7 +61,8 @@ def test_struct_layouts_match_header(tmp_path):
                    " offsetof(rtree_info_t, sort_children), (size_t)RTREE_PRUNE_ON); "
                    "printf(\"%zu %zu\\n\", offsetof(rtree_select_opts_t, order), (size_t)RTREE_ORDER_HILBERT); "
                    "printf(\"%zu %zu %zu\\n\", sizeof(rtree_tune_result_t), offsetof(rtree_tune_result_t, ms_all),"
-                   " offsetof(rtree_tune_result_t, order_all)); return 0;}\n")
+                   " offsetof(rtree_tune_result_t, order_all)); "
+                   "printf(\"%zu %zu\\n\", sizeof(rtree_allocator_t), offsetof(rtree_allocator_t, ctx)); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
@@ -73,28 +74,34 @@ def test_struct_layouts_match_header(tmp_path):
             C.sizeof(rt.rtree_join_opts_t), rt.rtree_info_t.sort_children.offset, rt.PRUNES["on"],
             rt.rtree_select_opts_t.order.offset, rt.ORDERS["hilbert"],
             C.sizeof(rt.rtree_tune_result_t), rt.rtree_tune_result_t.ms_all.offset,
-            rt.rtree_tune_result_t.order_all.offset]
+            rt.rtree_tune_result_t.order_all.offset,
+            C.sizeof(rt.rtree_allocator_t), rt.rtree_allocator_t.ctx.offset]
     assert got == want
 
 
 def test_argument_errors_need_no_gpu(lib):
     from paper_2309_16913_gb300 import rtree as rt
     # NULL out-pointer and bad sizes are rejected before any CUDA call.
-    assert lib.rtree_build(None, None, 0, None, None, None) == rt.RTREE_EINVAL
+    assert lib.rtree_build(None, None, 0, None, None, None, None) == rt.RTREE_EINVAL
     assert b"out is NULL" in lib.rtree_last_error()
     out = C.c_void_p()
-    assert lib.rtree_build(None, None, -1, None, None, C.byref(out)) == rt.RTREE_EINVAL
+    assert lib.rtree_build(None, None, -1, None, None, None, C.byref(out)) == rt.RTREE_EINVAL
     cfg = rt.rtree_config_t()
     cfg.fanout = 3
-    assert lib.rtree_build(None, None, 0, C.byref(cfg), None, C.byref(out)) == rt.RTREE_EINVAL
+    assert lib.rtree_build(None, None, 0, C.byref(cfg), None, None, C.byref(out)) == rt.RTREE_EINVAL
     assert b"fanout" in lib.rtree_last_error()
     assert lib.rtree_range_select(None, None, 0, None, None, C.byref(out)) == rt.RTREE_EINVAL
     assert lib.rtree_join(None, None, None, C.byref(out)) == rt.RTREE_EINVAL
     assert lib.rtree_join_ex(None, None, None, None, C.byref(out)) == rt.RTREE_EINVAL
     cfg = rt.rtree_config_t()
     cfg.sort_children = 2
-    assert lib.rtree_build(None, None, 0, C.byref(cfg), None, C.byref(out)) == rt.RTREE_EINVAL
+    assert lib.rtree_build(None, None, 0, C.byref(cfg), None, None, C.byref(out)) == rt.RTREE_EINVAL
     assert b"sort_children" in lib.rtree_last_error()
+    half = rt.rtree_allocator_t()  # an allocator needs both functions
+    half.alloc = rt.ALLOC_FN(lambda n, s, c: 0)
+    assert lib.rtree_build(None, None, 0, None, C.byref(half), None, C.byref(out)) == rt.RTREE_EINVAL
+    assert b"allocator" in lib.rtree_last_error()
+    assert lib.rtree_result_wait(None) == rt.RTREE_EINVAL
     assert lib.rtree_result_total(None) == 0
     lib.rtree_free(None)
     lib.rtree_result_free(None)
