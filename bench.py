@@ -513,9 +513,9 @@ def run_ours(args):
 
         e2e_run(2)
         k2 = max(2, min(args.steps, 6))
-        # the host link is shared and its rate drifts: three timed runs, the median reported
+        # the host link is shared and its rate drifts: five timed runs, the median reported
         runs = []
-        for _ in range(3):
+        for _ in range(5):
             barrier(world)
             t0 = time.perf_counter()
             e2e_run(k2)
@@ -528,7 +528,7 @@ def run_ours(args):
                "runs": [round(r, 1) for r in runs],
                "note": "build + select per step from pinned host inputs to pinned host results; "
                        "two steps in flight (double-buffered results), all copies inside the timed "
-                       "region; median of three runs of `steps` steps"}
+                       "region; median of five runs of `steps` steps"}
 
     # ---- batched uneven select: graph-captured plans vs one query per launch
     uneven = None
