@@ -246,9 +246,12 @@ RTREE_API rtree_status rtree_range_select(const rtree_t *tree, const float *quer
  * batched form of the select).
  *
  * A plan owns every device buffer a sorted select needs, sized for at most
- * max_queries queries and max_ids result ids per batch, and records the whole
- * device pipeline of rtree_range_select (count pass, scans, descriptor pass,
- * segmented sort, copy of the totals) as one CUDA graph per batch-size bucket
+ * max_queries queries and max_ids result ids per batch (and, for the
+ * warp-per-query mapping, 2*max_ids + 4*F*max_queries leaf-hit slots: its
+ * sizing pass stops above the leaves and reserves F slots per leaf a query
+ * meets), and records the whole
+ * device pipeline of rtree_range_select (sizing pass, scans, descriptor pass,
+ * segmented sort, store of the totals) as one CUDA graph per batch-size bucket
  * (powers of two from 256 up to max_queries); a batch is padded to its bucket
  * with NaN queries, which match nothing.  Unlike rtree_range_select, a run
  * needs no host round trip between kernels, so small batches cost one graph

@@ -40,6 +40,7 @@ struct rtree_plan {
     int device = 0;
     int mapping = RTREE_MAP_WARP_PER_QUERY;
     int64_t max_q = 0, ids_cap = 0;
+    int64_t leaf_cap = 0;  // leaf-hit slots: the bound pass reserves F per intersecting leaf
     float4 *queries = nullptr;
     rt::SelectBuffers b{};
     void *block = nullptr;            // one device allocation holding the buffers
@@ -86,6 +87,9 @@ void free_plan(rtree_plan *p)
 rtree_status allocate(rtree_plan *p)
 {
     const int64_t Q = p->max_q, C = p->ids_cap;
+    // slots exceed hits: about 2x on large queries, up to F per hit on tiny ones
+    const int64_t LC = 2 * C + 4 * (int64_t)p->tree->fanout * Q;
+    p->leaf_cap = LC;
     const long long wq_cap = Q + (Q > (1 << 20) ? Q : (1 << 20));
     struct Piece {
         void **dst;
@@ -100,7 +104,7 @@ rtree_status allocate(rtree_plan *p)
         {reinterpret_cast<void **>(&b.off), (size_t)(Q + 1) * 8},
         {reinterpret_cast<void **>(&b.off_leaf), (size_t)(Q + 1) * 8},
         {reinterpret_cast<void **>(&b.off_rng), (size_t)(Q + 1) * 8},
-        {reinterpret_cast<void **>(&b.leaf), (size_t)C * 4},
+        {reinterpret_cast<void **>(&b.leaf), (size_t)LC * 4},
         {reinterpret_cast<void **>(&b.rng), (size_t)C * 8},
         {reinterpret_cast<void **>(&b.ids), (size_t)C * 4},
         {reinterpret_cast<void **>(&b.cursors), (size_t)Q * 8},
@@ -131,7 +135,8 @@ rtree_status allocate(rtree_plan *p)
         *pc.dst = at;
         at += (pc.bytes + 255) & ~(size_t)255;
     }
-    b.leaf_cap = b.rng_cap = b.ids_cap = C;
+    b.rng_cap = b.ids_cap = C;
+    b.leaf_cap = LC;
     b.wq_cap = wq_cap;
     RT_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&p->host), 64, cudaHostAllocMapped | cudaHostAllocPortable));
     memset(p->host, 0, 64);
@@ -302,11 +307,12 @@ rtree_status rtree_plan_run(rtree_plan_t *p, const float *queries, int64_t q, vo
         *total = tot;
         if (fl[0] & 4)
             return fail(RTREE_ETIMEOUT, "rtree_plan_run: a work-queue wait exceeded its limit");
-        if (tot > p->ids_cap || tleaf > p->ids_cap || trng > p->ids_cap)
+        if (tot > p->ids_cap || tleaf > p->leaf_cap || trng > p->ids_cap)
             return fail(RTREE_EOVERFLOW,
-                        "rtree_plan_run: the batch needs %lld ids (%lld leaf hits, %lld ranges) but the "
-                        "plan holds %lld; results are incomplete",
-                        (long long)tot, (long long)tleaf, (long long)trng, (long long)p->ids_cap);
+                        "rtree_plan_run: the batch needs %lld ids (%lld leaf-hit slots, %lld ranges) but "
+                        "the plan holds %lld ids and %lld slots; results are incomplete",
+                        (long long)tot, (long long)tleaf, (long long)trng, (long long)p->ids_cap,
+                        (long long)p->leaf_cap);
         if (fl[0] || fl[1])
             return fail(RTREE_EINTERNAL, "rtree_plan_run: device flags 0x%x / 0x%x", fl[0], fl[1]);
         return RTREE_OK;

@@ -1287,9 +1287,12 @@ rtree_status select_enqueue(const rtree *t, const float4 *queries, int64_t Q, in
         RT_TRY(launch_wq(PASS_COUNT, t, queries, Q, io, b.flags, s, nullptr, b.wq_items, b.wq_cap,
                          b.wq_ctl));
     } else {
-        RT_TRY(launch(PASS_COUNT, t, queries, Q, io, b.ctr, b.flags, s));
+        // warp per query: the bound pass (stopped above the leaves) sizes the
+        // leaf-hit slots; the descriptor pass reports the exact counts
+        RT_TRY(launch(PASS_BOUND, t, queries, Q, io, b.ctr, b.flags, s));
     }
-    RT_TRY(scan_exclusive(b.cnt, b.off, Q, s));
+    if (wq)
+        RT_TRY(scan_exclusive(b.cnt, b.off, Q, s));
     RT_TRY(scan_exclusive(b.cnt_leaf, b.off_leaf, Q, s));
     RT_TRY(scan_exclusive(b.cnt_rng, b.off_rng, Q, s));
     SelIO so = unlimited();
@@ -1306,11 +1309,15 @@ rtree_status select_enqueue(const rtree *t, const float4 *queries, int64_t Q, in
         RT_TRY(launch_wq(PASS_DESC, t, queries, Q, so, b.flags, s, nullptr, b.wq_items, b.wq_cap,
                          b.wq_ctl));
     } else {
+        so.counts = b.cnt;            // exact ids per query
+        so.counts_leaf = b.cnt_leaf;  // exact leaf hits (the slot bounds are scanned already)
         RT_TRY(launch(PASS_DESC, t, queries, Q, so, b.ctr + 1, b.flags, s));
+        RT_TRY(scan_exclusive(b.cnt, b.off, Q, s));
     }
     SortSources src{};
     src.leaf = b.leaf;
     src.off_leaf = b.off_leaf;
+    src.leaf_len = wq ? nullptr : b.cnt_leaf;
     src.rng = b.rng;
     src.off_rng = b.off_rng;
     src.tree_ids = t->ids;
