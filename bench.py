@@ -547,12 +547,12 @@ def run_ours(args):
         jr = torch.from_numpy(j.rects).to(dev)
         js = torch.from_numpy(j.rects_s).to(dev)
 
-        def jstep(sort_children=False, prune="off"):
+        def jstep(sort_children=False, prune="off", traversal="auto"):
             a = rt.RTree(jr, None, fanout=32, stream=stream, sort_children=sort_children)
             b = rt.RTree(js, None, fanout=32, stream=stream, sort_children=sort_children)
-            r = a.join(b, stream=stream, prune=prune)
+            r = a.join(b, stream=stream, prune=prune, traversal=traversal)
             tot = r.total
-            r.close(); a.close(); b.close()
+            r.close(stream); a.close(stream); b.close(stream)
             return tot
 
         def jtime(**kw):
@@ -575,12 +575,19 @@ def run_ours(args):
             torch.cuda.synchronize()
             rt.rtree_timing_enable(False)
             k = rt.rtree_timing_get()
-            trav = sum(v[1] for n, v in k.items() if n.startswith("join_"))
+            trav = sum(v[1] for n, v in k.items() if n.startswith("join_") or n.startswith("jq_"))
             return pairs, ms, trav, {n: v for n, v in k.items() if n.startswith("join_") and v[0]}
 
         pairs, jms, jtrav, jk = jtime()
         ppairs, pms, ptrav, pk = jtime(sort_children=True, prune="on")
         assert ppairs == pairs
+        # the two schedules of the traversal, plain and pruned
+        sched = {}
+        for trv in ("levels", "queue"):
+            for pr in ("off", "on"):
+                p_, ms_, tr_, _ = jtime(sort_children=pr == "on", prune=pr, traversal=trv)
+                assert p_ == pairs
+                sched[f"{trv}_prune_{pr}"] = {"ms_per_step": round(ms_, 3), "traversal_ms": round(tr_, 3)}
         a = rt.RTree(jr, None, fanout=32, stream=stream, sort_children=True)
         b = rt.RTree(js, None, fanout=32, stream=stream, sort_children=True)
         jstats = a.join_stats(b, stream=stream, prune="off")
@@ -589,6 +596,7 @@ def run_ours(args):
                 "value": round(pairs * world / (jms / 1e3), 1), "unit": "pairs/s",
                 "pairs": int(pairs), "ms_per_step": round(jms, 3),
                 "traversal_ms": round(jtrav, 3),
+                "schedules": sched,
                 "join_stats": jstats,
                 "roofline": join_roofline(jstats, 32, 32, jk, hbm, peak_kind, clk),
                 "pruned": {"what": "sorted-children trees, O3 + O4/O5 pruned join (Section 4.2)",

@@ -470,15 +470,32 @@ RTREE_API rtree_status rtree_join(const rtree_t *r, const rtree_t *s, void *stre
  * of all 32 lanes packed densely onto the warp.  The result is identical to
  * rtree_join's.
  *
- * opts NULL -> RTREE_PRUNE_AUTO.  Errors: as rtree_join, and RTREE_EINVAL
- * for RTREE_PRUNE_ON when either tree was built without sort_children.
+ * opts NULL -> RTREE_PRUNE_AUTO, RTREE_JOIN_AUTO.  Errors: as rtree_join, and
+ * RTREE_EINVAL for RTREE_PRUNE_ON when either tree was built without
+ * sort_children, or an unknown option; RTREE_ETIMEOUT if a bounded
+ * work-queue wait ran out (RTREE_JOIN_QUEUE).
  */
 enum { RTREE_PRUNE_AUTO = 0, /* prune when both trees have sorted children */
        RTREE_PRUNE_OFF = 1,  /* plain one-to-many comparison */
        RTREE_PRUNE_ON = 2 };
+/* How the node pairs of the traversal are scheduled (same pairs either way). */
+enum { RTREE_JOIN_AUTO = 0,   /* the library's choice (RTREE_JOIN_LEVELS: faster on the joins measured;
+                                 the queue's counters see one atomic per node pair or more, while a
+                                 level costs one launch and one host read) */
+       RTREE_JOIN_LEVELS = 1, /* one launch per tree level over that level's node pairs, the pairs
+                                 found on one level being the next level's work (count, scan and
+                                 scatter per level; the call returns when its work has finished) */
+       RTREE_JOIN_QUEUE = 2 };/* a persistent grid pulls node pairs from a device work queue and
+                                 publishes the qualifying child pairs to it; a count pass, one host
+                                 read of the total, a scatter pass and the pair sort.  The call
+                                 returns with the scatter pass and sort in flight on `stream`
+                                 (rtree_result_wait).  If the traversal needs more node pairs
+                                 than the queue holds (8 per node of the two trees, at least
+                                 4M), the join is redone by levels */
 typedef struct rtree_join_opts {
-    int32_t prune; /* RTREE_PRUNE_* */
-    int32_t reserved[7];
+    int32_t prune;     /* RTREE_PRUNE_* */
+    int32_t traversal; /* RTREE_JOIN_* */
+    int32_t reserved[6];
 } rtree_join_opts_t;
 RTREE_API rtree_status rtree_join_ex(const rtree_t *r, const rtree_t *s, const rtree_join_opts_t *opts,
                                      void *stream, rtree_result_t **out);
@@ -511,7 +528,7 @@ RTREE_API rtree_status rtree_result_copy_to_host(const rtree_result_t *res, int6
  * returns its status: RTREE_OK, RTREE_EINTERNAL if a device-side consistency
  * check failed, RTREE_ETIMEOUT if a bounded work-queue wait ran out (the
  * result is then incomplete).  Results of calls that return only after their
- * work has finished (rtree_join) return RTREE_OK at once. */
+ * work has finished (a join by levels) return RTREE_OK at once. */
 RTREE_API rtree_status rtree_result_wait(const rtree_result_t *res);
 
 /* Releases a result (after the whole device has finished; the buffers go
@@ -600,9 +617,10 @@ RTREE_API long long rtree_launch_count(void);
  * on the host, before cudaMallocAsync is called; no GPU fault is involved. */
 RTREE_API void rtree_debug_fail_alloc_after(long long k);
 
-/* Testing hook for the bounded waits of the work-queue mapping
- * (RTREE_MAP_WORK_QUEUE): the next work-queue pass launched by any host
- * thread limits each device-side wait for work to `cycles` GPU clock cycles
+/* Testing hook for the bounded waits of the device work queues (the
+ * select's RTREE_MAP_WORK_QUEUE and the join's RTREE_JOIN_QUEUE): the next
+ * work-queue pass launched by any host thread (for the join, its count pass)
+ * limits each device-side wait for work to `cycles` GPU clock cycles
  * (<= 0: the default, about one second), and with hold != 0 it counts one
  * work item that is never published, so the pass cannot end by running out
  * of work: every waiting warp's wait runs out, the warp records the timeout

@@ -19,6 +19,17 @@ static thread_local std::string g_err;
 static std::atomic<long long> g_alloc_countdown{-1};  // < 0: no injected failure
 thread_local const rtree_allocator_t *t_alloc = nullptr;
 
+// Test hook (rtree_debug_wq_wait): the next work-queue pass waits at most
+// this many cycles and, with hold, counts one item that is never published.
+static std::atomic<long long> g_dbg_wait_cycles{0};
+static std::atomic<int> g_dbg_hold{0};
+
+void debug_wq_take(long long *cycles, int *hold)
+{
+    *cycles = g_dbg_wait_cycles.exchange(0);
+    *hold = g_dbg_hold.exchange(0);
+}
+
 rtree_status fail(rtree_status st, const char *fmt, ...)
 {
     char buf[512];
@@ -237,6 +248,12 @@ const char *rtree_version(void) { return "rtree-gb300 0.1 (sm_103a)"; }
 
 // Test hook: make the k-th following device allocation fail (k = -1 disables).
 void rtree_debug_fail_alloc_after(long long k) { g_alloc_countdown.store(k); }
+
+void rtree_debug_wq_wait(long long cycles, int hold)
+{
+    g_dbg_wait_cycles.store(cycles > 0 ? cycles : 0);
+    g_dbg_hold.store(hold != 0);
+}
 
 rtree_status rtree_build(const float *rects, const int32_t *ids, int64_t n,
                          const rtree_config_t *cfg, const rtree_allocator_t *alloc, void *stream,
@@ -641,6 +658,12 @@ rtree_status join_impl(const rtree_t *r, const rtree_t *s_tree, const rtree_join
     const bool both_sorted = r->sorted && s_tree->sorted;
     if (prune == RTREE_PRUNE_ON && !both_sorted)
         return fail(RTREE_EINVAL, "rtree_join: pruning needs both trees built with sort_children");
+    const int traversal = opts ? opts->traversal : RTREE_JOIN_AUTO;
+    if (traversal < RTREE_JOIN_AUTO || traversal > RTREE_JOIN_QUEUE)
+        return fail(RTREE_EINVAL, "rtree_join: unknown traversal %d", traversal);
+    // the counters come from the level-by-level form, which is also the
+    // default (measured faster than the queued form on the 2M x 2M join)
+    const bool queued = !stats && traversal == RTREE_JOIN_QUEUE;
     try {
         DeviceGuard guard(r->device);
         AllocScope scope(r->allocator());
@@ -653,10 +676,19 @@ rtree_status join_impl(const rtree_t *r, const rtree_t *s_tree, const rtree_join
         rtree_status st = tree_ready_on(r, s);
         if (st == RTREE_OK)
             st = tree_ready_on(s_tree, s);
-        if (st == RTREE_OK)
-            st = tree_join(r, s_tree, prune != RTREE_PRUNE_OFF && both_sorted, s, res, stats);
-        if (st == RTREE_OK) {
-            cudaError_t e = cudaStreamSynchronize(s);
+        const bool pr = prune != RTREE_PRUNE_OFF && both_sorted;
+        bool by_levels = !queued;
+        if (st == RTREE_OK && queued)
+            st = tree_join_queue(r, s_tree, pr, s, res, &by_levels);
+        if (st == RTREE_OK && by_levels) {
+            st = tree_join(r, s_tree, pr, s, res, stats);
+            if (st == RTREE_OK) {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess)
+                    st = fail(RTREE_ECUDA, "rtree_join: %s", cudaGetErrorString(e));
+            }
+        } else if (st == RTREE_OK) {  // launch errors; the rest is reported by rtree_result_wait
+            cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess)
                 st = fail(RTREE_ECUDA, "rtree_join: %s", cudaGetErrorString(e));
         }

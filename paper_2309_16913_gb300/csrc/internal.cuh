@@ -33,6 +33,11 @@ void clear_error();
             return s_;                                                                     \
     } while (0)
 
+// Takes (and clears) the rtree_debug_wq_wait setting for the next
+// work-queue pass: a wait limit in cycles (0: the default) and whether to
+// count one never-published item.
+void debug_wq_take(long long *cycles, int *hold);
+
 // ------------------------------------------------------------------ memory
 // The device-memory hook of the call in progress on this host thread (the
 // tree's allocator), or null for the stream-ordered pool of the current
@@ -417,6 +422,13 @@ void mailbox_put_deferred(Mailbox *m);
 // Enqueues the copy kernel on s, then records m.ev on s.
 rtree_status mailbox_post(const Mailbox &m, const PostList &l, cudaStream_t s);
 rtree_status mailbox_wait(const Mailbox &m);
+// Posts two device words (flags) to a new mailbox of `res`, behind the work
+// enqueued on s so far; rtree_result_wait reads them (word 0 bit 4: a
+// bounded device wait ran out; any other bit: a consistency check failed).
+rtree_status post_result_status(const int32_t *flags, cudaStream_t s, rtree_result *res);
+// Reads nwords <= kMailboxWords device words listed in l on the host (one
+// kernel stores them into a mailbox; the host waits for its event).
+rtree_status read_words(const PostList &l, cudaStream_t s, uint32_t *out, int nwords);
 struct MailboxRef {
     Mailbox m;
     MailboxRef() = default;
@@ -464,6 +476,13 @@ rtree_status select_stats(const rtree *t, const float4 *queries, int64_t q, cuda
 // at the leaves [3], and the pairs found [4].
 rtree_status tree_join(const rtree *r, const rtree *s_tree, bool prune, cudaStream_t s,
                        rtree_result *res, int64_t *stats = nullptr);
+// The same join with the node pairs pulled by a persistent grid from a device
+// work queue (count pass, one host read of the total, scatter pass, sort);
+// returns with the scatter pass and sort in flight (the result's status
+// mailbox gets their flags).  *redo_by_levels is set (and nothing produced)
+// when the traversal needs more node pairs than the queue holds.
+rtree_status tree_join_queue(const rtree *r, const rtree *s_tree, bool prune, cudaStream_t s,
+                             rtree_result *res, bool *redo_by_levels);
 
 }  // namespace rt
 

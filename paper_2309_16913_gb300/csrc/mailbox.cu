@@ -117,4 +117,39 @@ rtree_status mailbox_wait(const Mailbox &m)
     return RTREE_OK;
 }
 
+rtree_status post_result_status(const int32_t *flags, cudaStream_t s, rtree_result *res)
+{
+    Mailbox *mb = new Mailbox();
+    rtree_status st = mailbox_get(mb);
+    if (st != RTREE_OK) {
+        delete mb;
+        return st;
+    }
+    PostList pl{};
+    pl.src[0] = flags;
+    pl.words[0] = 2;
+    pl.at[0] = 0;
+    pl.n = 1;
+    st = mailbox_post(*mb, pl, s);
+    if (st != RTREE_OK) {
+        cudaEventSynchronize(mb->ev);
+        mailbox_put(mb);
+        delete mb;
+        return st;
+    }
+    res->status = mb;
+    return RTREE_OK;
+}
+
+rtree_status read_words(const PostList &l, cudaStream_t s, uint32_t *out, int nwords)
+{
+    MailboxRef mb;
+    RT_TRY(mailbox_get(&mb.m));
+    RT_TRY(mailbox_post(mb.m, l, s));
+    RT_TRY(mailbox_wait(mb.m));
+    for (int i = 0; i < nwords; ++i)
+        out[i] = ((const volatile uint32_t *)mb.m.h)[i];
+    return RTREE_OK;
+}
+
 }  // namespace rt

@@ -351,11 +351,7 @@ struct WorkQueue {
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr long long kWaitCycles = 2000000000LL;  // about one second
 
-// Test hook (rtree_debug_wq_wait): the next work-queue launch waits at most
-// g_dbg_wait_cycles and, with g_dbg_hold, counts one item that is never
-// published.
-std::atomic<long long> g_dbg_wait_cycles{0};
-std::atomic<int> g_dbg_hold{0};
+
 
 __device__ __forceinline__ unsigned long long pack_item(int q, int node)
 {
@@ -648,8 +644,9 @@ rtree_status launch_wq(int pass, const rtree *t, const float4 *q, int64_t Q, con
         items_p = items.p;
         ctl_p = ctl.p;
     }
-    const long long dbg_wait = g_dbg_wait_cycles.exchange(0);
-    const int dbg_hold = g_dbg_hold.exchange(0);
+    long long dbg_wait = 0;
+    int dbg_hold = 0;
+    debug_wq_take(&dbg_wait, &dbg_hold);
     {
         KernelTimer kt_("wq_init", s);
         int64_t b = (cap_items + 255) / 256;
@@ -680,47 +677,7 @@ SelIO unlimited()
     return io;
 }
 
-// Reads n <= 8 device words of the listed sources on the host: one kernel
-// stores them into a mailbox, the host waits for its event (never behind
-// copies other calls queued on a copy engine).
-rtree_status read_words(const PostList &l, cudaStream_t s, uint32_t *out, int nwords)
-{
-    MailboxRef mb;
-    RT_TRY(mailbox_get(&mb.m));
-    RT_TRY(mailbox_post(mb.m, l, s));
-    RT_TRY(mailbox_wait(mb.m));
-    for (int i = 0; i < nwords; ++i)
-        out[i] = ((const volatile uint32_t *)mb.m.h)[i];
-    return RTREE_OK;
-}
-
 int64_t word64(const uint32_t *w) { return (int64_t)((uint64_t)w[0] | ((uint64_t)w[1] << 32)); }
-
-// Posts the select and sort flags (2 words) to the result's status mailbox
-// behind the call's last kernel; rtree_result_wait reads them.
-rtree_status post_status(const int32_t *flags, cudaStream_t s, rtree_result *res)
-{
-    Mailbox *mb = new Mailbox();
-    rtree_status st = mailbox_get(mb);
-    if (st != RTREE_OK) {
-        delete mb;
-        return st;
-    }
-    PostList pl{};
-    pl.src[0] = flags;
-    pl.words[0] = 2;
-    pl.at[0] = 0;
-    pl.n = 1;
-    st = mailbox_post(*mb, pl, s);
-    if (st != RTREE_OK) {
-        cudaEventSynchronize(mb->ev);
-        mailbox_put(mb);
-        delete mb;
-        return st;
-    }
-    res->status = mb;
-    return RTREE_OK;
-}
 
 rtree_status empty_result(int64_t Q, DevBuf<int64_t> &off, cudaStream_t s, rtree_result *res)
 {
@@ -832,7 +789,7 @@ rtree_status range_select_bounded(const rtree *t, const float4 *queries, int64_t
     src.tree_ids = t->ids;
     RT_TRY(segmented_sort_gather(ids.p, off.p, Q, total, src, s, flags.p + 1));
     // the sort runs on in the order of s; its flags reach the result's status
-    RT_TRY(post_status(flags.p, s, res));
+    RT_TRY(post_result_status(flags.p, s, res));
     res->total = total;
     res->offsets = off.release();
     res->ids = ids.release();
@@ -977,7 +934,7 @@ rtree_status range_select(const rtree *t, const float4 *queries, int64_t Q, bool
     }
     // the second pass (and sort) run on in the order of s; their flags reach
     // the result's status
-    RT_TRY(post_status(flags.p, s, res));
+    RT_TRY(post_result_status(flags.p, s, res));
     res->total = total;
     res->offsets = off.release();
     res->ids = ids.release();
@@ -1366,9 +1323,3 @@ rtree_status select_stats(const rtree *t, const float4 *queries, int64_t Q, cuda
 }
 
 }  // namespace rt
-
-extern "C" void rtree_debug_wq_wait(long long cycles, int hold)
-{
-    rt::g_dbg_wait_cycles.store(cycles > 0 ? cycles : 0);
-    rt::g_dbg_hold.store(hold != 0);
-}

@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "RTREE_OK", 1: "RTREE_EINVAL", 2: "RTREE_ENOMEM", 3: "RTREE_E
 LAYOUTS = {"soa": 0, "aos": 1, "lohi": 2}
 MAPPINGS = {"auto": 0, "warp_per_query": 1, "work_queue": 2}
 PRUNES = {"auto": 0, "off": 1, "on": 2}
+TRAVERSALS = {"auto": 0, "levels": 1, "queue": 2}
 ORDERS = {"input": 0, "hilbert": 1}
 
 
@@ -45,7 +46,7 @@ class rtree_config_t(C.Structure):
 
 
 class rtree_join_opts_t(C.Structure):
-    _fields_ = [("prune", C.c_int32), ("reserved", C.c_int32 * 7)]
+    _fields_ = [("prune", C.c_int32), ("traversal", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class rtree_select_opts_t(C.Structure):
@@ -494,11 +495,14 @@ def rtree_join(r_handle: int, s_handle: int, stream=None) -> int:
     return out.value
 
 
-def rtree_join_ex(r_handle: int, s_handle: int, prune: str | int = "auto", stream=None) -> int:
-    """rtree_join with the sorted-node prunings ("auto", "off" or "on")."""
+def rtree_join_ex(r_handle: int, s_handle: int, prune: str | int = "auto", stream=None,
+                  traversal: str | int = "auto") -> int:
+    """rtree_join with the sorted-node prunings ("auto", "off" or "on") and the
+    traversal schedule ("auto", "levels" or "queue")."""
     lib = load_library()
     opts = rtree_join_opts_t()
     opts.prune = PRUNES[prune] if isinstance(prune, str) else int(prune)
+    opts.traversal = TRAVERSALS[traversal] if isinstance(traversal, str) else int(traversal)
     out = C.c_void_p()
     _check(lib.rtree_join_ex(r_handle, s_handle, C.byref(opts), _stream(stream), C.byref(out)), lib)
     return out.value
@@ -896,10 +900,12 @@ class RTree:
     def select_stats(self, queries, stream=None) -> dict:
         return rtree_range_select_stats(self.handle, queries, stream)
 
-    def join(self, other: "RTree", stream=None, prune: str | int | None = None) -> Result:
-        if prune is None:
+    def join(self, other: "RTree", stream=None, prune: str | int | None = None,
+             traversal: str | int | None = None) -> Result:
+        if prune is None and traversal is None:
             return Result(rtree_join(self.handle, other.handle, stream), self.allocator)
-        return Result(rtree_join_ex(self.handle, other.handle, prune, stream), self.allocator)
+        return Result(rtree_join_ex(self.handle, other.handle, prune or "auto", stream, traversal or "auto"),
+                      self.allocator)
 
     def join_stats(self, other: "RTree", stream=None, prune: str | int = "auto") -> dict:
         return rtree_join_stats(self.handle, other.handle, prune, stream)
