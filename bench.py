@@ -413,9 +413,8 @@ def run_ours(args):
         step(F, layout, mapping, order)
     torch.cuda.synchronize()
 
-    # ---- timed region
+    # ---- timed region (no per-kernel events inside it)
     rt.rtree_timing_reset()
-    rt.rtree_timing_enable(True)
     launches0 = rt.rtree_launch_count()
     clocks = ClockSampler(local)
     clocks.start()
@@ -430,12 +429,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    rt.rtree_timing_enable(False)
     ms_total = ev0.elapsed_time(ev1)
     launches = rt.rtree_launch_count() - launches0
-    kern = rt.rtree_timing_get()
     ms_max = max_over_ranks(ms_total, world, dev)
     value = Q * args.steps * world / (ms_max / 1e3)
+
+    # ---- per-kernel breakdown: the same steps again with CUDA events around
+    # every launch (and around the sort's span), outside the timed region
+    rt.rtree_timing_reset()
+    rt.rtree_timing_enable(True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        step(F, layout, mapping, order)
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    rt.rtree_timing_enable(False)
+    kern = rt.rtree_timing_get()
+    ms_instrumented = ev2.elapsed_time(ev3)
 
     # ---- roofline of the dominant kernel; query-order comparison on the same tree
     with rt.RTree(rects, ids, fanout=F, layout=layout) as t:
@@ -449,15 +461,15 @@ def run_ours(args):
     persist = None if args.no_persist else run_persist(rt, torch, rects, ids, queries, F, layout, rank)
     algo = algorithmic_bytes(stats, F, Q, seg)
     hbm, peak_kind = peaks()
-    # share = the kernel's event time over the step's wall time (the sort's
-    # class kernels overlap one another, so their shares can add up past 1;
-    # sort_all is their span)
+    # share = the kernel's event time over the instrumented steps' wall time
+    # (the sort's class kernels overlap one another, so their shares can add
+    # up past 1; sort_all is their span)
     breakdown = {}
     for name, (n_l, ms) in kern.items():
         if n_l == 0:
             continue
         entry = {"launches": n_l, "ms_per_step": round(ms / args.steps, 3),
-                 "share": round(ms / max(1e-9, ms_total), 4)}
+                 "share": round(ms / max(1e-9, ms_instrumented), 4)}
         if name in algo and ms > 0:
             entry["gbs"] = round(algo[name] / (ms / args.steps / 1e3) / 1e9, 1)
         breakdown[name] = entry
@@ -625,6 +637,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (rects 160 MB, tree ~200 MB; no flush)",
                        "sweep_ms_per_step": sweep, "seed": seed},
             "gpu_launches": int(launches),
+            "ms_per_step_instrumented": round(ms_instrumented / args.steps, 3),
             "clocks": clk,
             "roofline": roofline,
             "roofline_node_test": roofline_node_test,

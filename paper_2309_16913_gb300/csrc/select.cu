@@ -150,6 +150,32 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         __syncwarp();
         return;
     }
+    if (PASS == PASS_BOUND && K == 1 && !leaf && m.x >= t.leaf_base) {
+        // the bound pass at a node whose children are leaves: an intersecting
+        // leaf inside the query is counted whole, any other reserves F slots;
+        // nothing is pushed (one node per step: the test is warp-uniform)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int j = sub + c * G;
+            const bool hit = j < m.y && meets(b[c], q);
+            const bool cont = hit && inside(b[c], q);
+            const int r = F * __popc(__ballot_sync(RT_FULL, hit && !cont));
+            wk.lcur += r;
+            wk.cur += r;
+            const unsigned mc = __ballot_sync(RT_FULL, cont);
+            if (mc) {
+                int n = 0;
+                if (cont) {
+                    const int4 cm = __ldg(t.meta + m.x + j);
+                    n = cm.w - cm.z;
+                }
+                wk.rcur += __popc(mc);
+                wk.cur += __reduce_add_sync(RT_FULL, (unsigned)n);
+            }
+        }
+        __syncwarp();
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int j = sub + c * G;
