@@ -187,13 +187,14 @@ def test_long_segments_msd_and_skewed_fallback(rt):
 
 
 @pytest.mark.parametrize("case", ["ragged", "crowded", "crowded_20k", "over_128k", "two_values",
-                                  "one_value", "both_signs_mid"])
+                                  "one_value", "both_signs_mid", "large_buckets"])
 def test_sort_edge_cases(rt, case):
     """Per-query sort edges: a segment just above 16384 ids (ragged), a
     dense id run with far outliers (crowded buckets, at 60k and at 20k ids),
     a segment over 131072 ids, duplicate ids (two values; one value, all
     keys equal), and mid-size segments whose ids straddle zero (value-range
-    buckets must not crowd)."""
+    buckets must not crowd), and a 40953-id segment whose value buckets all
+    hold 17 ids (every warp takes the 32-key network)."""
     everything = np.array([[-INF, -INF, INF, INF]], np.float32)
     rng = np.random.default_rng(13)
     queries = everything
@@ -221,6 +222,11 @@ def test_sort_edge_cases(rt, case):
         n = 30_000
         ids = np.where(np.arange(n) % 2 == 0, 7, 8).astype(np.int32)
         rects = random_case("uniform", n, 24)
+    elif case == "large_buckets":
+        ids = (64 * np.arange(2409)[:, None] + np.arange(17)[None, :]).astype(np.int32).ravel()
+        ids = rng.permutation(ids)
+        n = ids.size
+        rects = random_case("uniform", n, 28)
     elif case == "one_value":
         n = 20_000
         ids = np.full(n, -5, np.int32)
