@@ -176,6 +176,68 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         __syncwarp();
         return;
     }
+    if (PASS == PASS_DESC && !WQ && F == 64 && node >= 0 && !leaf && m.x >= t.leaf_base) {
+        // the descriptor pass at a node whose children are leaves: a leaf
+        // inside the query is emitted as its id range, and the other
+        // intersecting leaves are visited here, one after another from the
+        // ballot, instead of through the stack (the sort makes the order of
+        // the hits immaterial).  Measured faster at F=64 only (with six
+        // CTAs per SM); at F=32 and F=128 the stack form is faster.
+        unsigned mv[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int j = sub + c * G;
+            const bool hit = j < m.y && meets(b[c], q);
+            const bool cont = hit && inside(b[c], q);
+            mv[c] = __ballot_sync(RT_FULL, hit && !cont);
+            const unsigned mc = __ballot_sync(RT_FULL, cont);
+            if (mc) {
+                int lo = 0, hi = 0;
+                if (cont) {
+                    const int4 cm = __ldg(t.meta + m.x + j);
+                    lo = cm.z;
+                    hi = cm.w;
+                }
+                const int64_t o = sg.rbase + wk.rcur + __popc(mc & lt);
+                if (cont && o < sg.rlim && o < io.rng_cap)
+                    io.rng_out[o] = make_int2(lo, hi);
+                wk.rcur += __popc(mc);
+                wk.cur += __reduce_add_sync(RT_FULL, (unsigned)(hi - lo));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            unsigned mm = mv[c];
+            while (mm) {
+                const int lf = m.x + c * G + __ffs(mm) - 1;
+                mm &= mm - 1;
+                float4 e[C];
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc)
+                    e[cc] = load_entry_t<F, LAYOUT>(t.mbr, lf, sub + cc * G);
+                const int4 lm = __ldg(t.meta + lf);
+                if (stats) {
+                    ++wk.n_visit;
+                    ++wk.n_leaf;
+                }
+#pragma unroll
+                for (int cc = 0; cc < C; ++cc) {
+                    const int jj = sub + cc * G;
+                    const bool emit = jj < lm.y && meets(e[cc], q);
+                    const unsigned me = __ballot_sync(RT_FULL, emit);
+                    if (me) {
+                        const int64_t o = sg.lbase + wk.lcur + __popc(me & lt);
+                        if (emit && o < sg.llim && o < io.leaf_cap)
+                            io.leaf_out[o] = __ldg(t.ids + lm.x + jj);
+                    }
+                    wk.cur += __popc(me);
+                    wk.lcur += __popc(me);
+                }
+            }
+        }
+        __syncwarp();
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const int j = sub + c * G;
@@ -283,10 +345,17 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, const Wal
     atomicAdd(stats + 5, (unsigned long long)(wk.cur - wk.lcur));
 }
 
+// CTAs per SM the warp-per-query kernel is compiled for.  The descriptor
+// pass at F=64 takes six (40 registers a thread): its walk is bound by the
+// latency of dependent node loads, and the extra resident warps were
+// measured to outweigh a few spilled registers; elsewhere the compiler
+// chooses.
+constexpr int select_min_blocks(int F, int pass) { return pass == PASS_DESC && F == 64 ? 6 : 1; }
+
 // Warp per query: each warp takes the next query from a counter and walks
 // its whole subtree.
 template <int F, int LAYOUT, int PASS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, select_min_blocks(F, PASS))
     k_select(TreeDev t, const float4 *__restrict__ queries, int64_t Q, SelIO io,
              unsigned long long *__restrict__ next_query, int32_t *__restrict__ flags, int cap,
              unsigned long long *__restrict__ stats)
