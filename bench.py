@@ -189,20 +189,33 @@ KERNEL_SOURCES = {"select_count": ["select.cu", "internal.cuh"], "select_bound":
                   "scatter": ["radix_sort.cu"], "join_count": ["join.cu", "internal.cuh"]}
 
 
-def ncu_traffic(kernel: str):
+def config_matches(kv, fanout, layout=None):
+    """A summary line taken at one fanout (and node layout) serves only a run
+    in that configuration."""
+    if fanout is not None and "fanout" in kv and int(kv["fanout"]) != fanout:
+        return False
+    return layout is None or "layout" not in kv or kv["layout"] == layout
+
+
+def ncu_traffic(kernel: str, fanout=None, layout=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel; else None."""
+    on the current source of that kernel (and in this configuration); else
+    None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None, None
     want = source_sha(KERNEL_SOURCES.get(kernel, []))
+    note = None
     for line in open(path):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
         if kv.get("kernel") == kernel and kv.get("workload") == WORKLOAD:
-            if kv.get("source_sha") == want:
+            if not config_matches(kv, fanout, layout):
+                note = note or "no capture in this configuration"
+            elif kv.get("source_sha") == want:
                 return float(kv["bytes_per_step"]), kv.get("note")
-            return None, "kernel changed since the ncu capture"
-    return None, None
+            else:
+                note = "kernel changed since the ncu capture"
+    return None, note
 
 
 def algorithmic_bytes(stats, F, Q, seg_sizes):
@@ -270,13 +283,13 @@ def join_roofline(st, Fr, Fs, kern, hbm, peak_kind, clk):
            "frac": round(achieved / hbm, 4), "peak_kind": peak_kind, "ms_per_step": round(ms, 4),
            "algorithmic_bytes_per_step": int(algo), "node_pairs": int(visited),
            "predicate_tests_per_s": round(2 * tests / (ms / 1e3), 1)}
-    issue = issue_fraction([n for n in names], visited, ms, clk)
+    issue = issue_fraction([n for n in names], visited, ms, clk, fanout=Fr)
     if issue:
         out["issue"] = issue
     return out
 
 
-def node_test_roofline(kern, algo, stats, steps, hbm, peak_kind, clk):
+def node_test_roofline(kern, algo, stats, steps, hbm, peak_kind, clk, F, layout):
     """Per node-test kernel: the logical rate (algorithmic bytes, upper tree
     levels included though L2 serves them), the DRAM rate from ncu's DRAM
     bytes per node visit on the profile case scaled to this run's visits,
@@ -292,12 +305,12 @@ def node_test_roofline(kern, algo, stats, steps, hbm, peak_kind, clk):
         logical = algo[k] / (ms / 1e3) / 1e9
         e = {"ms_per_step": round(ms, 4), "node_visits": int(units[k]),
              "logical_gbs": round(logical, 1), "logical_frac": round(logical / hbm, 4)}
-        m = ncu_metrics(k)
+        m = ncu_metrics(k, F, layout)
         if m is not None and "dram_bytes_per_unit" in m:
             dram = float(m["dram_bytes_per_unit"]) * units[k] / (ms / 1e3) / 1e9
             e["dram_gbs"] = round(dram, 1)
             e["dram_frac"] = round(dram / hbm, 4)
-        iss = issue_fraction([k], units[k], ms, clk)
+        iss = issue_fraction([k], units[k], ms, clk, fanout=F, layout=layout)
         if iss:
             e["issue"] = iss
         fr = {"hbm": e.get("dram_frac"), "issue": (iss or {}).get("frac")}
@@ -316,28 +329,29 @@ def node_test_roofline(kern, algo, stats, steps, hbm, peak_kind, clk):
     return out
 
 
-def ncu_metrics(kernel: str):
+def ncu_metrics(kernel: str, fanout=None, layout=None):
     """Instruction and DRAM counters of `kernel` from the committed ncu
-    summary, if taken on the current source of that kernel; else None."""
+    summary, if taken on the current source of that kernel (and in this
+    configuration); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_metrics.txt")
     if not os.path.exists(path):
         return None
     want = source_sha(KERNEL_SOURCES.get(kernel, []))
     for line in open(path):
         kv = dict(re.findall(r"(\w+)=(\S+)", line))
-        if kv.get("kernel") == kernel:
-            return kv if kv.get("source_sha") == want else None
+        if kv.get("kernel") == kernel and config_matches(kv, fanout, layout) and kv.get("source_sha") == want:
+            return kv
     return None
 
 
-def issue_fraction(kernels, units, ms, clk, sms=152, schedulers=4):
+def issue_fraction(kernels, units, ms, clk, sms=152, schedulers=4, fanout=None, layout=None):
     """Issue-slot use of kernels that process `units` work units in `ms`:
     instructions per unit (ncu, profile case) * units / (issue slots per
     second * time).  Issue slots per second = SMs * 4 schedulers * the
     median SM clock sampled during the timed region."""
     inst_per_unit = 0.0
     for k in kernels:
-        m = ncu_metrics(k)
+        m = ncu_metrics(k, fanout, layout)
         if m is None or "inst_per_unit" not in m:
             return None
         inst_per_unit += float(m["inst_per_unit"])
@@ -389,7 +403,7 @@ def run_ours(args):
 
     # ---- pick fanout / layout / mapping / traversal order with the library's
     # autotuner (one build + sorted select per configuration, CUDA-event timed)
-    fanouts = [args.fanout] if args.fanout else [16, 32, 64]
+    fanouts = [args.fanout] if args.fanout else [16, 32, 64, 128]
     if args.no_tune:
         if not args.fanout or "auto" in (args.layout, args.mapping, args.order):
             raise SystemExit("--no-tune needs --fanout, --layout, --mapping and --order")
@@ -480,7 +494,7 @@ def run_ours(args):
     n_l, ms = kern[dominant]
     ms_step = ms / args.steps  # the kernel's time in one step, all its launches
     achieved = algo[dominant] / (ms_step / 1e3) / 1e9
-    traffic, traffic_note = ncu_traffic(dominant)
+    traffic, traffic_note = ncu_traffic(dominant, F, layout)
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4), "peak_kind": peak_kind,
                 "launches_per_step": n_l // args.steps,
@@ -494,7 +508,7 @@ def run_ours(args):
                             "segments over 40960; bound by shared-memory work and per-segment latency, not by HBM "
                             "(ncu: 45-53% issue active, a few % of DRAM peak)")
     # the node-test kernels, each against HBM (ncu DRAM bytes) and issue slots
-    roofline_node_test = node_test_roofline(kern, algo, stats, args.steps, hbm, peak_kind, clk)
+    roofline_node_test = node_test_roofline(kern, algo, stats, args.steps, hbm, peak_kind, clk, F, layout)
 
     # ---- end to end through the C ABI with host (pinned) buffers
     e2e = None

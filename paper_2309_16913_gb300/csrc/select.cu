@@ -176,13 +176,14 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         __syncwarp();
         return;
     }
-    if (PASS == PASS_DESC && !WQ && F == 64 && node >= 0 && !leaf && m.x >= t.leaf_base) {
+    if (PASS == PASS_DESC && !WQ && (F == 64 || F == 128) && node >= 0 && !leaf && m.x >= t.leaf_base) {
         // the descriptor pass at a node whose children are leaves: a leaf
         // inside the query is emitted as its id range, and the other
         // intersecting leaves are visited here, one after another from the
         // ballot, instead of through the stack (the sort makes the order of
-        // the hits immaterial).  Measured faster at F=64 only (with six
-        // CTAs per SM); at F=32 and F=128 the stack form is faster.
+        // the hits immaterial).  Measured faster at F=64 and F=128 (with
+        // the CTAs per SM of select_min_blocks); at F=32 the stack form is
+        // faster.
         unsigned mv[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -348,9 +349,12 @@ __device__ __forceinline__ void flush_stats(unsigned long long *stats, const Wal
 // CTAs per SM the warp-per-query kernel is compiled for.  The descriptor
 // pass at F=64 takes six (40 registers a thread): its walk is bound by the
 // latency of dependent node loads, and the extra resident warps were
-// measured to outweigh a few spilled registers; elsewhere the compiler
-// chooses.
-constexpr int select_min_blocks(int F, int pass) { return pass == PASS_DESC && F == 64 ? 6 : 1; }
+// measured to outweigh a few spilled registers; at F=128 four (64
+// registers, no spills); elsewhere the compiler chooses.
+constexpr int select_min_blocks(int F, int pass)
+{
+    return pass != PASS_DESC ? 1 : (F == 64 ? 6 : (F == 128 ? 4 : 1));
+}
 
 // Warp per query: each warp takes the next query from a counter and walks
 // its whole subtree.
