@@ -3,8 +3,8 @@ configuration (the same C ABI calls bench.py times).
 
 At 10M rectangles every one of the million queries is compared exactly with
 the oracle, whose select runs on all host cores (orc_select_mt), in chunks
-of 65536 queries: at the benchmark's configuration (F=64, AoS, Hilbert
-order) and at F=16 SoA in input order; the uneven mix (100k queries, 1%
+of 65536 queries: at the configurations the benchmark's autotuner picks
+(F=128 LOHI and F=64 AoS, Hilbert order) and at F=16 SoA in input order; the uneven mix (100k queries, 1%
 heavy) is compared in full too.  The remaining fanout/layout pairs are
 checked for properties that hold at any size (a valid CSR, strictly
 ascending id lists within the id range) and on a seeded sample.  The
@@ -82,7 +82,7 @@ def compare_all(t_gpu, t_orc, queries, context, **select_kw):
         res.close()
 
 
-@pytest.mark.parametrize("F,layout,order", [(64, "aos", "hilbert"), (16, "soa", "input")])
+@pytest.mark.parametrize("F,layout,order", [(128, "lohi", "hilbert"), (64, "aos", "hilbert"), (16, "soa", "input")])
 def test_scaled_10m_every_query_exact(rt, F, layout, order):
     import torch
     w = dg.workload("scaled")
@@ -93,7 +93,7 @@ def test_scaled_10m_every_query_exact(rt, F, layout, order):
     assert total > 10**9
 
 
-@pytest.mark.parametrize("F", [16, 32, 64])
+@pytest.mark.parametrize("F", [16, 32, 64, 128])
 def test_scaled_10m_1m_queries(rt, F):
     import torch
     w = dg.workload("scaled")
