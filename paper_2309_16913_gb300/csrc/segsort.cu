@@ -266,6 +266,7 @@ struct CtaSmem {
     uint32_t wsum[W];
     uint32_t red0[W], red1[W];  // per-warp partial reductions
     uint32_t crowded;
+    long long claim;  // the list entry this CTA takes next
 };
 
 // Exclusive block scan of one int per thread (uses sm.wsum); returns the
@@ -579,19 +580,27 @@ __device__ __forceinline__ void push_large(const LongList &lg, int32_t seg, int6
 // One CTA per listed segment.  BUCKETS: the list holds SegDesc entries whose
 // keys sit in `scratch`; otherwise segment ids whose ids are gathered from S.
 // ITEMS keys per thread; a segment of more than 16384 ids whose buckets are
-// crowded goes to the MSD path.
+// crowded goes to the MSD path.  CTAs claim list entries from the counter
+// *next (zero at launch), so a CTA that drew short segments takes more.
 template <int THREADS, bool BUCKETS, int ITEMS = kItems>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_sort_cta(const void *__restrict__ list, const unsigned long long *__restrict__ count,
                int64_t list_cap, const int64_t *__restrict__ off, SortSources S,
                const uint32_t *__restrict__ scratch, int32_t *__restrict__ out,
                SegDesc *__restrict__ crowded, unsigned long long *__restrict__ n_crowded,
-               int64_t crowded_cap, LongList lg)
+               int64_t crowded_cap, LongList lg, unsigned long long *__restrict__ next)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CtaSmem<THREADS, ITEMS> &sm = *reinterpret_cast<CtaSmem<THREADS, ITEMS> *>(smem_raw);
     const int64_t cnt = list_len(count, list_cap);
-    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0)
+            sm.claim = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const int64_t b = sm.claim;
+        __syncthreads();  // every thread has read the claim before the next one is written
+        if (b >= cnt)
+            break;
         int64_t dof;
         int n;
         if (BUCKETS) {
@@ -1037,8 +1046,8 @@ struct Crowded {
 template <int THREADS, bool BUCKETS, int ITEMS = kItems>
 rtree_status launch_cta(const void *list, const unsigned long long *count, int64_t list_cap,
                         const int64_t *off, const SortSources &S, const uint32_t *scratch,
-                        int32_t *out, const Crowded &cr, cudaStream_t s, const char *name,
-                        const LongList &lg = LongList{})
+                        int32_t *out, const Crowded &cr, unsigned long long *next, cudaStream_t s,
+                        const char *name, const LongList &lg = LongList{})
 {
     if (list_cap <= 0)
         return RTREE_OK;
@@ -1052,7 +1061,7 @@ rtree_status launch_cta(const void *list, const unsigned long long *count, int64
         grid = list_cap;
     KernelTimer kt_(name, s);
     kern<<<(unsigned)grid, THREADS, bytes, s>>>(list, count, list_cap, off, S, scratch, out, cr.list,
-                                                cr.count, cr.cap, lg);
+                                                cr.count, cr.cap, lg, next);
     RT_LAUNCH();
     return RTREE_OK;
 }
@@ -1183,8 +1192,11 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
     DevBuf<unsigned long long> hdr(s);
     RT_TRY(lists.alloc((size_t)C_COUNT * nseg, "sort lists"));
     RT_TRY(large_tmp.alloc(nseg, "sort lists"));
-    RT_TRY(hdr.alloc(HDR_WORDS + 2, "sort counters"));
-    RT_CUDA(cudaMemsetAsync(hdr.p, 0, (HDR_WORDS + 2) * sizeof(unsigned long long), s));
+    // the header, two crowded-list counters, and one claim counter per CTA-sort launch
+    constexpr int kClaims = 6;
+    RT_TRY(hdr.alloc(HDR_WORDS + 2 + kClaims, "sort counters"));
+    RT_CUDA(cudaMemsetAsync(hdr.p, 0, (HDR_WORDS + 2 + kClaims) * sizeof(unsigned long long), s));
+    auto claim = [&](int k) { return hdr.p + HDR_WORDS + 2 + k; };
     const int sms = sm_count();
     {
         int64_t blocks = (nseg + 255) / 256;
@@ -1229,7 +1241,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
         const cudaStream_t s2 = fk.side(2);
         const LongList lg{L(C_LARGE), large_tmp.p, hdr.p};
         RT_TRY((launch_cta<1024, false, kItemsBig>(L(C_CTA40K), H(C_CTA40K), cap_of(kCtaMax + 1), offsets, S,
-                                                   nullptr, out, cr1, s2, "sort_cta", lg)));
+                                                   nullptr, out, cr1, claim(0), s2, "sort_cta", lg)));
         // Long segments: gather into place, MSD-partition into the scratch
         // area, then sort the buckets back into place.
         const int64_t grid = max_large < (int64_t)sms * 2 ? max_large : (int64_t)sms * 2;
@@ -1248,7 +1260,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
             RT_LAUNCH();
         }
         const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
-        RT_TRY((launch_cta<512, true, kItemsMid>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, s2, "sort_bucket")));
+        RT_TRY((launch_cta<512, true, kItemsMid>(buckets.p, H(HDR_BUCKETS), desc_cap, nullptr, S, scratch.p, out, cr2, claim(1), s2, "sort_bucket")));
         RT_TRY(launch_lsd(cr2, out, s2));
         {
             int64_t g2 = desc_cap < (int64_t)sms * 4 ? desc_cap : (int64_t)sms * 4;
@@ -1258,11 +1270,11 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
             RT_LAUNCH();
         }
     }
-    RT_TRY((launch_cta<512, false, M>(L(C_CTA16K), H(C_CTA16K), cap_of(8193), offsets, S, nullptr, out, cr1, s, "sort_cta")));
+    RT_TRY((launch_cta<512, false, M>(L(C_CTA16K), H(C_CTA16K), cap_of(8193), offsets, S, nullptr, out, cr1, claim(2), s, "sort_cta")));
     const cudaStream_t s1 = fk.side(1), s0 = fk.side(0);
-    RT_TRY((launch_cta<256, false, M>(L(C_CTA8K), H(C_CTA8K), cap_of(4097), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
-    RT_TRY((launch_cta<128, false, M>(L(C_CTA4K), H(C_CTA4K), cap_of(2049), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
-    RT_TRY((launch_cta<64, false, M>(L(C_CTA2K), H(C_CTA2K), cap_of(257), offsets, S, nullptr, out, cr1, s1, "sort_cta")));
+    RT_TRY((launch_cta<256, false, M>(L(C_CTA8K), H(C_CTA8K), cap_of(4097), offsets, S, nullptr, out, cr1, claim(3), s1, "sort_cta")));
+    RT_TRY((launch_cta<128, false, M>(L(C_CTA4K), H(C_CTA4K), cap_of(2049), offsets, S, nullptr, out, cr1, claim(4), s1, "sort_cta")));
+    RT_TRY((launch_cta<64, false, M>(L(C_CTA2K), H(C_CTA2K), cap_of(257), offsets, S, nullptr, out, cr1, claim(5), s1, "sort_cta")));
     RT_TRY(launch_warp<8>(L(C_W8), H(C_W8), cap_of(129), offsets, S, out, s0));
     RT_TRY(launch_warp<4>(L(C_W4), H(C_W4), cap_of(65), offsets, S, out, s0));
     RT_TRY(launch_warp<2>(L(C_W2), H(C_W2), cap_of(33), offsets, S, out, s0));
