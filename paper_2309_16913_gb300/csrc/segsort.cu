@@ -767,13 +767,22 @@ __global__ void __launch_bounds__(1024, 1)
 __global__ void __launch_bounds__(1024)
     k_gather_large(const int32_t *__restrict__ list, const unsigned long long *__restrict__ count,
                    int64_t list_cap, const int64_t *__restrict__ tmp_off, int64_t scratch_cap,
-                   const int64_t *__restrict__ off, SortSources S, int32_t *__restrict__ out)
+                   const int64_t *__restrict__ off, SortSources S, int32_t *__restrict__ out,
+                   unsigned long long *__restrict__ next)
 {
     const int64_t cnt = list_len(count, list_cap);
     __shared__ int32_t rstart[1024];
     __shared__ int32_t wsum[32];
+    __shared__ long long claim;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0)
+            claim = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const int64_t b = claim;
+        __syncthreads();
+        if (b >= cnt)
+            break;
         const int32_t i = list[b];
         int32_t *dst = out + off[i];
         if (tmp_off[b] + (off[i + 1] - off[i]) > scratch_cap)
@@ -833,13 +842,22 @@ __global__ void __launch_bounds__(1024)
                     int64_t scratch_cap, const int64_t *__restrict__ off,
                     const uint32_t *__restrict__ ids, uint32_t *__restrict__ scratch,
                     SegDesc *__restrict__ buckets, SegDesc *__restrict__ oversize, int64_t desc_cap,
-                    unsigned long long *__restrict__ hdr, int32_t *__restrict__ flags)
+                    unsigned long long *__restrict__ hdr, int32_t *__restrict__ flags,
+                    unsigned long long *__restrict__ next)
 {
     const int64_t cnt = list_len(count, list_cap);
     __shared__ uint32_t hist[kBins], cursor[kBins];
     __shared__ uint32_t red_and[32], red_or[32];
+    __shared__ long long claim;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t b = blockIdx.x; b < cnt; b += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0)
+            claim = (long long)atomicAdd(next, 1ull);
+        __syncthreads();
+        const int64_t b = claim;
+        __syncthreads();
+        if (b >= cnt)
+            break;
         const int32_t seg = list[b];
         const int64_t o = off[seg];
         const int64_t n = off[seg + 1] - o;
@@ -1193,7 +1211,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
     RT_TRY(lists.alloc((size_t)C_COUNT * nseg, "sort lists"));
     RT_TRY(large_tmp.alloc(nseg, "sort lists"));
     // the header, two crowded-list counters, and one claim counter per CTA-sort launch
-    constexpr int kClaims = 6;
+    constexpr int kClaims = 8;
     RT_TRY(hdr.alloc(HDR_WORDS + 2 + kClaims, "sort counters"));
     RT_CUDA(cudaMemsetAsync(hdr.p, 0, (HDR_WORDS + 2 + kClaims) * sizeof(unsigned long long), s));
     auto claim = [&](int k) { return hdr.p + HDR_WORDS + 2 + k; };
@@ -1248,7 +1266,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
         {
             KernelTimer kt_("sort_gather", s2);
             k_gather_large<<<(unsigned)grid, 1024, 0, s2>>>(L(C_LARGE), H(C_LARGE), max_large, large_tmp.p,
-                                                            scratch_cap, offsets, S, out);
+                                                            scratch_cap, offsets, S, out, claim(6));
             RT_LAUNCH();
         }
         {
@@ -1256,7 +1274,7 @@ rtree_status segmented_sort_gather(int32_t *out, const int64_t *offsets, int64_t
             k_msd_partition<<<(unsigned)grid, 1024, 0, s2>>>(
                 L(C_LARGE), large_tmp.p, H(C_LARGE), max_large, scratch_cap, offsets,
                 reinterpret_cast<const uint32_t *>(out), scratch.p, buckets.p, oversize.p, desc_cap,
-                hdr.p, flags);
+                hdr.p, flags, claim(7));
             RT_LAUNCH();
         }
         const Crowded cr2{crowded2.p, n_crowded + 1, desc_cap};
