@@ -38,7 +38,7 @@ constexpr int kItemsMid = 32;           // keys per thread of the CTA sorts up t
 constexpr int kItemsBig = 40;           // keys per thread of the CTA sort above kCtaMax
 constexpr int kCtaBigMax = 1024 * kItemsBig;
 constexpr uint32_t kSign = 0x80000000u;
-constexpr int kBucketBitsMax = 12;      // at most 4096 buckets
+constexpr int kBucketBitsMax = 13;      // at most 8192 buckets
 constexpr int kBucketDensity = 1;       // 2^(ceil(log2 n) - 1) buckets of the key range
 constexpr int kBucketCrowded = 32;      // a longer bucket sends the segment to LSD
 
@@ -246,7 +246,7 @@ constexpr int log2_floor(int v) { return v > 1 ? 1 + log2_floor(v / 2) : 0; }
 template <int THREADS, int ITEMS = kItems>
 struct CtaSmem {
     static constexpr int W = THREADS / 32;
-    // at most 2^(ceil(log2 n) - 1) <= n/2 buckets are used (and at most 2^12)
+    // at most 2^(ceil(log2 n) - 1) <= n/2 buckets are used (and at most 2^13)
     static constexpr int kCntBits = log2_floor(THREADS * ITEMS / 2) < kBucketBitsMax
                                         ? log2_floor(THREADS * ITEMS / 2) : kBucketBitsMax;
     uint32_t buf[THREADS * ITEMS];
@@ -437,8 +437,9 @@ __device__ __forceinline__ void bucket_network(uint32_t *buf, int s0, int c)
 
 // Sorts the n <= THREADS*kItems keys in sm.buf and writes them to dst (xor
 // kSign back to ids).  Keys are bucketed by value, (key - min) >> shift with
-// B = ceil(log2 n) - 1 bits (at most 12) of the key range, using shared
-// atomics, so a bucket of spread-out keys holds one to four keys; each
+// B = ceil(log2 n) - 1 bits (at most 13) of the key range, using shared
+// atomics, so a bucket of spread-out keys holds one to a few keys (about
+// five on average for the 40960-id class); each
 // bucket is then sorted in registers.  Measuring from the minimum keeps a
 // range that straddles a power of two (e.g. ids around 2^k, or of both
 // signs) from crowding into a few buckets.
@@ -469,7 +470,7 @@ __device__ __forceinline__ bool cta_bucket_sort(CtaSmem<THREADS, ITEMS> &sm, int
         __syncthreads();
         return true;
     }
-    // bucket = (key - kmin) >> shift: B = ceil(log2 n) - 1 bits (at most 12)
+    // bucket = (key - kmin) >> shift: B = ceil(log2 n) - 1 bits (at most 13)
     // of the key range, so only buckets inside [kmin, kmax] exist
     const uint32_t span = kmax - kmin;
     const int width = 32 - __clz(span);
