@@ -520,38 +520,52 @@ def run_ours(args):
         h_off = [torch.empty(Q + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
         h_out = [torch.empty(max(1, int(total_hits)), dtype=torch.int32).pin_memory() for _ in range(2)]
 
-        def e2e_run(steps):
+        def e2e_run(steps, log=None):
             # per step: host rects/ids/queries in, host offsets/ids out.  Each
             # select returns once its work and copies are enqueued
             # (rtree_range_select_host_async); the previous step's results are
             # waited for after the next step has started, so its copies to
-            # host memory overlap the next build and select.
+            # host memory overlap the next build and select.  `log` gets the
+            # host time of each step's build call, select call and wait for
+            # the previous step's results (ms).
             pending = None
             for k in range(steps):
+                a = time.perf_counter()
                 h = rt.rtree_build(h_rects, h_ids, F, layout, stream)
+                b = time.perf_counter()
                 p = rt.rtree_range_select_host_async(h, h_q, h_off[k % 2], h_out[k % 2], mapping=mapping,
                                                      order=order, stream=stream)
+                c = time.perf_counter()
                 rt.rtree_free(h, stream=stream)
                 if pending is not None:
                     assert pending.wait() == total_hits
                 pending = p
+                if log is not None:
+                    log.append([round((b - a) * 1e3, 1), round((c - b) * 1e3, 1),
+                                round((time.perf_counter() - c) * 1e3, 1)])
+            a = time.perf_counter()
             assert pending.wait() == total_hits
+            if log is not None:
+                log.append([0.0, 0.0, round((time.perf_counter() - a) * 1e3, 1)])
 
         e2e_run(2)
         k2 = max(2, min(args.steps, 6))
         # the host link is shared and its rate drifts: five timed runs, the median reported
-        runs = []
+        runs, step_logs = [], []
         for _ in range(5):
             barrier(world)
+            log = []
             t0 = time.perf_counter()
-            e2e_run(k2)
+            e2e_run(k2, log)
             torch.cuda.synchronize()
             el = max_over_ranks(time.perf_counter() - t0, world, dev)
             runs.append(Q * k2 * world / el)
+            step_logs.append(log)
         e2e = {"value": round(float(np.median(runs)), 1), "unit": UNIT,
                "h2d_bytes_per_step": int(w.rects.nbytes + w.ids.nbytes + w.queries.nbytes),
                "d2h_bytes_per_step": int(8 * (Q + 1) + 4 * int(total_hits)), "steps": k2,
                "runs": [round(r, 1) for r in runs],
+               "host_ms_per_step": step_logs,  # per run: [build call, select call, wait for the previous step]
                "note": "build + select per step from pinned host inputs to pinned host results; "
                        "two steps in flight (double-buffered results), all copies inside the timed "
                        "region; median of five runs of `steps` steps"}
