@@ -344,6 +344,22 @@ __global__ void k_layout(int F, int layout, int64_t P, int64_t m,
     }
 }
 
+// part = {position of a short leaf (-1: none), its count, short leaves}:
+// every leaf whose count is not F records itself (part starts {-1, 0, 0}).
+__global__ void k_leaf_part(const int4 *__restrict__ leaf_meta, int64_t P, int F,
+                            unsigned long long *__restrict__ part)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int c = leaf_meta[s].y;
+        if (c != F) {
+            part[0] = (unsigned long long)s;
+            part[1] = (unsigned long long)c;
+            atomicAdd(part + 2, 1ull);
+        }
+    }
+}
+
 __global__ void k_ranges_leaf(int4 *__restrict__ meta, int64_t g_base, int64_t P)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P;
@@ -644,6 +660,25 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     t->nbox = nbox.release();
     t->ids = ids_out.release();
     t->bytes = (int64_t)nodes * F * 16 + nodes * 32 + n * 4;
+    return compute_leaf_part(t, s);
+}
+
+rtree_status compute_leaf_part(rtree *t, cudaStream_t s)
+{
+    if (t->levels == 0)
+        return RTREE_OK;
+    DevBuf<int64_t> part(s);
+    RT_TRY(part.alloc(3, "leaf record"));
+    RT_CUDA(cudaMemsetAsync(part.p, 0xff, sizeof(int64_t), s));
+    RT_CUDA(cudaMemsetAsync(part.p + 1, 0, 2 * sizeof(int64_t), s));
+    const int64_t P = t->level_nodes[t->levels - 1];
+    {
+        KernelTimer kt_("leaf_part", s);
+        k_leaf_part<<<blocks_for(P), kThreads, 0, s>>>(t->meta + t->level_base[t->levels - 1], P, t->fanout,
+                                                       reinterpret_cast<unsigned long long *>(part.p));
+        RT_LAUNCH();
+    }
+    t->leaf_part = part.release();
     return RTREE_OK;
 }
 

@@ -175,10 +175,12 @@ void free_tree_arrays(rtree *t, cudaStream_t s, bool ordered)
     release(t->meta, a, s, ordered);
     release(t->nbox, a, s, ordered);
     release(t->ids, a, s, ordered);
+    release(t->leaf_part, a, s, ordered);
     t->mbr = nullptr;
     t->meta = nullptr;
     t->nbox = nullptr;
     t->ids = nullptr;
+    t->leaf_part = nullptr;
     if (t->root_mb) {  // a kernel may still write it: reused only after its event
         mailbox_put_deferred(t->root_mb);
         delete t->root_mb;

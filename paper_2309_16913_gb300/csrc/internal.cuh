@@ -180,6 +180,11 @@ struct TreeDev {
     int32_t fanout;
     int32_t layout;
     int32_t sorted;  // entries of every node ascend by lx
+    // The leaf level's one short leaf: {its position among the leaves (-1:
+    // none), its count, how many leaves are short}.  With at most one short
+    // leaf, leaf s holds entries [s*F - (s > pos ? F - count : 0), + F or
+    // count) of the id array, without reading its metadata.
+    const int64_t *leaf_part;
 };
 
 }  // namespace rt
@@ -200,6 +205,7 @@ struct rtree {
     int4 *meta = nullptr;
     float4 *nbox = nullptr;
     int32_t *ids = nullptr;
+    int64_t *leaf_part = nullptr;  // see TreeDev::leaf_part
     float root_mbr[4] = {0, 0, 0, 0};  // valid once root_ready (see tree_root_box)
     bool root_ready = true;
     rt::Mailbox *root_mb = nullptr;     // the build's posted root box until it is read
@@ -220,6 +226,7 @@ struct rtree {
         v.fanout = fanout;
         v.layout = layout;
         v.sorted = sorted;
+        v.leaf_part = leaf_part;
         return v;
     }
 };
@@ -298,6 +305,10 @@ __device__ __forceinline__ float4 load_entry_t(const float *__restrict__ mbr, in
 rtree_status scan_exclusive(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 rtree_status scan_exclusive(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
 rtree_status scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Fills t->leaf_part (allocated here from the tree's allocator) from the
+// leaf level's metadata, on stream s.
+rtree_status compute_leaf_part(rtree *t, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs on key bits [bit_lo, bit_hi).
 // Inputs are not modified; outputs must not alias inputs.

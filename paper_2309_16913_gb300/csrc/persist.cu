@@ -420,7 +420,7 @@ rtree_status load_payload(FILE *f, const Header &h, rtree *t, cudaStream_t s)
     t->meta = meta.release();
     t->nbox = nbox.release();
     t->ids = ids.release();
-    return RTREE_OK;
+    return compute_leaf_part(t, s);
 }
 
 }  // namespace

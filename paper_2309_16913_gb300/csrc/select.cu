@@ -82,6 +82,40 @@ struct Seg {
     int64_t base, lim, lbase, llim, rbase, rlim;
 };
 
+// The leaf level's short leaf (TreeDev::leaf_part), read once per kernel;
+// ok: at most one short leaf, so leaf spans follow from positions.
+struct LeafPart {
+    int64_t pos;
+    int cnt;
+    bool ok;
+};
+
+__device__ __forceinline__ LeafPart leaf_part_of(const TreeDev &t)
+{
+    LeafPart lp{-1, 0, false};
+    if (t.leaf_part) {
+        lp.pos = __ldg(t.leaf_part);
+        lp.cnt = (int)__ldg(t.leaf_part + 1);
+        lp.ok = __ldg(t.leaf_part + 2) <= 1;
+    }
+    return lp;
+}
+
+// Entries [first, first + cnt) of the id array belong to leaf node g.
+template <int F>
+__device__ __forceinline__ void leaf_span(const TreeDev &t, const LeafPart &lp, int64_t g, int &first, int &cnt)
+{
+    if (lp.ok) {
+        const int64_t s = g - t.leaf_base;
+        cnt = s == lp.pos ? lp.cnt : F;
+        first = (int)(s * F - (lp.pos >= 0 && s > lp.pos ? F - lp.cnt : 0));
+    } else {
+        const int4 lm = __ldg(t.meta + g);
+        first = lm.x;
+        cnt = lm.y;
+    }
+}
+
 // Reserves n slots of a per-query cursor (lane 0 does the atomic).
 __device__ __forceinline__ int64_t reserve(int32_t *cursor, int n, int lane)
 {
@@ -100,7 +134,7 @@ template <int F, int LAYOUT, int PASS, bool WQ>
 __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, int32_t *st, int &top,
                                             int cap, const SelIO &io, int64_t qi, const Seg &sg,
                                             Walk &wk, bool stats, int lane, int grp, int sub,
-                                            unsigned lt)
+                                            unsigned lt, const LeafPart &lp)
 {
     constexpr int G = F < 32 ? F : 32;
     constexpr int K = 32 / G;
@@ -183,7 +217,8 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
         // ballot, instead of through the stack (the sort makes the order of
         // the hits immaterial).  Measured faster at F=64 and F=128 (with
         // the CTAs per SM of select_min_blocks); at F=32 the stack form is
-        // faster.
+        // faster.  Leaf spans come from the leaf's position (leaf_span), so a
+        // leaf's ids are requested with its entries.
         unsigned mv[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -195,9 +230,9 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
             if (mc) {
                 int lo = 0, hi = 0;
                 if (cont) {
-                    const int4 cm = __ldg(t.meta + m.x + j);
-                    lo = cm.z;
-                    hi = cm.w;
+                    int cn;
+                    leaf_span<F>(t, lp, m.x + j, lo, cn);
+                    hi = lo + cn;
                 }
                 const int64_t o = sg.rbase + wk.rcur + __popc(mc & lt);
                 if (cont && o < sg.rlim && o < io.rng_cap)
@@ -212,11 +247,16 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
             while (mm) {
                 const int lf = m.x + c * G + __ffs(mm) - 1;
                 mm &= mm - 1;
+                int first, cnt;
+                leaf_span<F>(t, lp, lf, first, cnt);
                 float4 e[C];
+                int32_t id[C];
 #pragma unroll
-                for (int cc = 0; cc < C; ++cc)
-                    e[cc] = load_entry_t<F, LAYOUT>(t.mbr, lf, sub + cc * G);
-                const int4 lm = __ldg(t.meta + lf);
+                for (int cc = 0; cc < C; ++cc) {
+                    const int jj = sub + cc * G;
+                    e[cc] = load_entry_t<F, LAYOUT>(t.mbr, lf, jj);
+                    id[cc] = jj < cnt ? __ldg(t.ids + first + jj) : 0;
+                }
                 if (stats) {
                     ++wk.n_visit;
                     ++wk.n_leaf;
@@ -224,12 +264,12 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
 #pragma unroll
                 for (int cc = 0; cc < C; ++cc) {
                     const int jj = sub + cc * G;
-                    const bool emit = jj < lm.y && meets(e[cc], q);
+                    const bool emit = jj < cnt && meets(e[cc], q);
                     const unsigned me = __ballot_sync(RT_FULL, emit);
                     if (me) {
                         const int64_t o = sg.lbase + wk.lcur + __popc(me & lt);
                         if (emit && o < sg.llim && o < io.leaf_cap)
-                            io.leaf_out[o] = __ldg(t.ids + lm.x + jj);
+                            io.leaf_out[o] = id[cc];
                     }
                     wk.cur += __popc(me);
                     wk.lcur += __popc(me);
@@ -370,6 +410,7 @@ __global__ void __launch_bounds__(kThreads, select_min_blocks(F, PASS))
     int32_t *st = smem + (threadIdx.x >> 5) * cap;
     const int grp = lane / G, sub = lane % G;
     const unsigned lt = lanemask_lt();
+    const LeafPart lp = PASS == PASS_DESC ? leaf_part_of(t) : LeafPart{-1, 0, false};
 
     for (;;) {
         unsigned long long qi = 0;
@@ -397,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, select_min_blocks(F, PASS))
                 break;
             }
             select_step<F, LAYOUT, PASS, false>(t, q, st, top, cap, io, (int64_t)qi, sg, wk,
-                                                stats != nullptr, lane, grp, sub, lt);
+                                                stats != nullptr, lane, grp, sub, lt, lp);
         }
         if (stats && lane == 0)
             flush_stats(stats, wk, true);
@@ -468,6 +509,7 @@ __global__ void __launch_bounds__(kThreads)
     int32_t *st = smem + (threadIdx.x >> 5) * cap;
     const int grp = lane / G, sub = lane % G;
     const unsigned lt = lanemask_lt();
+    const LeafPart lp{-1, 0, false};  // the work queue keeps leaves on the stack
 
     for (;;) {
         unsigned long long ticket = 0;
@@ -518,7 +560,7 @@ __global__ void __launch_bounds__(kThreads)
                 break;
             }
             select_step<F, LAYOUT, PASS, true>(t, q, st, top, cap, io, qi, sg, wk,
-                                               stats != nullptr, lane, grp, sub, lt);
+                                               stats != nullptr, lane, grp, sub, lt, lp);
             // donate the older half of the stack when other warps are waiting
             if (top >= 2 && (steps & 3) == 0) {
                 unsigned long long h = 0, tl = 0;
