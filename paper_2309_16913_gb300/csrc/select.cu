@@ -200,8 +200,8 @@ __device__ __forceinline__ void select_step(const TreeDev &t, const float4 q, in
             if (mc) {
                 int n = 0;
                 if (cont) {
-                    const int4 cm = __ldg(t.meta + m.x + j);
-                    n = cm.w - cm.z;
+                    int lo;
+                    leaf_span<F>(t, lp, m.x + j, lo, n);
                 }
                 wk.rcur += __popc(mc);
                 wk.cur += __reduce_add_sync(RT_FULL, (unsigned)n);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, select_min_blocks(F, PASS))
     int32_t *st = smem + (threadIdx.x >> 5) * cap;
     const int grp = lane / G, sub = lane % G;
     const unsigned lt = lanemask_lt();
-    const LeafPart lp = PASS == PASS_DESC ? leaf_part_of(t) : LeafPart{-1, 0, false};
+    const LeafPart lp = PASS == PASS_DESC || PASS == PASS_BOUND ? leaf_part_of(t) : LeafPart{-1, 0, false};
 
     for (;;) {
         unsigned long long qi = 0;
