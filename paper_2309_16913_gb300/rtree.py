@@ -657,7 +657,7 @@ def rtree_server_stop(server: int) -> None:
         load_library().rtree_server_stop(server)
 
 
-def rtree_autotune(rects, queries, ids=None, fanouts=(16, 32, 64), include_build: bool = True,
+def rtree_autotune(rects, queries, ids=None, fanouts=(16, 32, 64, 128), include_build: bool = True,
                    stream=None, orders: bool = False) -> dict:
     """Times every fanout x layout x mapping (x traversal order with
     ``orders``) on the given sample and returns the fastest configuration
