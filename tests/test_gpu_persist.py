@@ -150,3 +150,79 @@ def test_handmade_structure_is_refused(rt, tmp_path):
         struct.pack_into("<i", b, meta_off + 16 * node + field, value)
         e = damaged(rt, bad, reseal(b))
         assert e.status == rt.RTREE_EINVAL and "tree structure" in str(e), (node, field, value)
+
+
+def test_loaded_tree_with_two_short_leaves(rt, tmp_path):
+    """A loaded tree whose leaf level holds two short leaves: one entry is
+    moved across the boundary between the built tree's short leaf and a full
+    sibling (same parent), with the leaves' metadata, the entry boxes and the
+    parent's child box edited to match.  The traversal cannot derive leaf
+    spans from positions here and must read the leaves' metadata; selects
+    (small queries and queries that contain whole leaves) equal brute force."""
+    F, n = 64, 20000  # 313 leaves, the last packed one holding 32 entries
+    rects = random_case("uniform", n, 41)
+    ids = np.arange(n, dtype=np.int32) * 5 + 3
+    rng = np.random.default_rng(43)
+    lo = rng.random((40, 2)).astype(np.float32) * np.float32(0.6)
+    big = np.concatenate([lo, lo + np.float32(0.35)], axis=1).astype(np.float32)
+    q = np.concatenate([random_case("uniform", 600, 42), big,
+                        np.array([[-1, -1, 2, 2]], np.float32)]).astype(np.float32)
+    src = tmp_path / "built.rtree"
+    with rt.RTree(rects, ids, fanout=F, layout="aos") as t:
+        t.save(str(src))
+        info, level_nodes = t.info(), t.export()["level_nodes"]
+    M = info["nodes"]
+    base = np.concatenate([[0], np.cumsum(level_nodes)])
+    leaf_base, parent_base = int(base[-2]), int(base[-3])
+    buf = bytearray(src.read_bytes())
+    mbr_off = HEADER_BYTES
+    meta_off = mbr_off + M * F * 16
+    nbox_off = meta_off + M * 16
+    mbr = np.frombuffer(buf, np.float32, M * F * 4, mbr_off).reshape(M, F, 4).copy()
+    meta = np.frombuffer(buf, np.int32, M * 4, meta_off).reshape(M, 4).copy()
+    nbox = np.frombuffer(buf, np.float32, M * 4, nbox_off).reshape(M, 4).copy()
+    short = [g for g in range(leaf_base, M) if meta[g, 1] != F]
+    assert len(short) == 1
+    gs = short[0]
+    c = int(meta[gs, 1])
+    par = [p for p in range(parent_base, leaf_base) if meta[p, 0] <= gs < meta[p, 0] + meta[p, 1]][0]
+    empty = mbr[gs, F - 1].copy()
+
+    def grow(box, other):
+        return np.array([min(box[0], other[0]), min(box[1], other[1]),
+                         max(box[2], other[2]), max(box[3], other[3])], np.float32)
+    if gs - 1 >= meta[par, 0]:  # the donor precedes: its last entry opens the short leaf
+        d = gs - 1
+        moved = mbr[d, F - 1].copy()
+        mbr[d, F - 1] = empty
+        meta[d, 1] -= 1
+        meta[d, 3] -= 1
+        mbr[gs, 1:c + 1] = mbr[gs, 0:c].copy()
+        mbr[gs, 0] = moved
+        meta[gs, 0] -= 1
+        meta[gs, 2] -= 1
+    else:  # the donor follows: its first entry closes the short leaf
+        d = gs + 1
+        assert d < meta[par, 0] + meta[par, 1]
+        moved = mbr[d, 0].copy()
+        mbr[d, 0:F - 1] = mbr[d, 1:F].copy()
+        mbr[d, F - 1] = empty
+        meta[d, 0] += 1
+        meta[d, 2] += 1
+        meta[d, 1] -= 1
+        mbr[gs, c] = moved
+        meta[gs, 3] += 1
+    meta[gs, 1] += 1
+    slot = gs - meta[par, 0]
+    mbr[par, slot] = grow(mbr[par, slot], moved)
+    nbox[gs] = grow(nbox[gs], moved)
+    buf[mbr_off:meta_off] = mbr.tobytes()
+    buf[meta_off:nbox_off] = meta.tobytes()
+    buf[nbox_off:nbox_off + M * 16] = nbox.tobytes()
+    moved_file = tmp_path / "two_short.rtree"
+    moved_file.write_bytes(bytes(reseal(buf)))
+    with rt.RTree.load(str(moved_file)) as t2:
+        counts = t2.export()["counts"][leaf_base:]
+        assert np.count_nonzero(counts != F) == 2
+        sel = select_np(t2, q)
+    assert_csr_equal(sel, oracle.brute_select(rects, q, ids))
