@@ -9,16 +9,18 @@
 //                 swaps inside a lane);
 //   257..16384    one CTA of 64-512 threads (32 keys each), entirely in
 //                 shared memory:
-//                 bucket the keys by value within their range (1-4 keys per
-//                 bucket for spread-out ids) with shared atomics, then each
-//                 thread sorts whole buckets in registers with a bitonic
-//                 network; a crowded bucket sends the segment to a stable
-//                 LSD radix sort (8-bit digits);
+//                 bucket the keys by value within their range (at most 8192
+//                 buckets: a few keys each for spread-out ids) with shared
+//                 atomics, then each thread sorts whole buckets in registers
+//                 with a bitonic network; a crowded bucket sends the segment
+//                 to a stable LSD radix sort (8-bit digits);
 //   16385..40960  the same with one CTA of 1024 threads, 40 keys each (160 KB
 //                 of shared memory; a crowded one goes on to the next path);
 //   > 40960       gathered into place, partitioned by its top differing bits
 //                 into buckets of about 8K ids (MSD step through a scratch
 //                 area), each bucket then sorted like a mid-size segment.
+// Each class runs as a persistent grid whose CTAs claim segments from an
+// atomic counter, so CTAs that drew long segments do not hold up the rest.
 // LSD passes whose digit is equal for all keys are skipped (from the AND and
 // OR of the keys).  In each LSD pass a key's rank among equal digits comes
 // from walking the keys in order: each warp owns a contiguous run and takes it

@@ -32,7 +32,13 @@
 //   SCATTER  writes the ids themselves in traversal order (unsorted output);
 //   DESC     writes the leaf hits and, for every whole subtree, its (lo, hi)
 //            range of the tree's id array; the sorted output is then built
-//            by the segmented sort, which reads the ranges directly.
+//            by the segmented sort, which reads the ranges directly;
+//   BOUND    the count pass stopped above the leaves, sizing DESC's slots.
+// With warp per query at F = 64 and 128, DESC visits a leaf-parent's
+// intersecting leaves in place (no push, no pop) and derives each leaf's id
+// span from its position (STR fills every leaf but one, whose position the
+// build records), so a leaf costs one memory round trip: its entries and its
+// ids are requested together.
 #include <atomic>
 #include <cstring>
 
