@@ -215,13 +215,14 @@ __global__ void __launch_bounds__(kThreads, 4)
 // CTAs of the persistent grid: every SM full (at most one tile each).
 int grid_for(int64_t ntiles)
 {
-    static int per_sm = 0;
-    if (per_sm == 0) {
+    static const int per_sm = [] {  // initialised once, thread-safely
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_scatter, kThreads, 0) != cudaSuccess || v < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_scatter, kThreads, 0) != cudaSuccess || v < 1) {
+            cudaGetLastError();
             v = 1;
-        per_sm = v;
-    }
+        }
+        return v;
+    }();
     const int64_t g = (int64_t)per_sm * sm_count();
     return (int)(ntiles < g ? ntiles : g);
 }
