@@ -444,9 +444,9 @@ __global__ void __launch_bounds__(kThreads, select_min_blocks(F, PASS))
                 break;
             }
             select_step<F, LAYOUT, PASS, false>(t, q, st, top, cap, io, (int64_t)qi, sg, wk,
-                                                stats != nullptr, lane, grp, sub, lt, lp);
+                                                PASS == PASS_COUNT && stats != nullptr, lane, grp, sub, lt, lp);
         }
-        if (stats && lane == 0)
+        if (PASS == PASS_COUNT && stats && lane == 0)
             flush_stats(stats, wk, true);
         if (lane == 0) {
             if (wk.overflow)
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kThreads)
                 break;
             }
             select_step<F, LAYOUT, PASS, true>(t, q, st, top, cap, io, qi, sg, wk,
-                                               stats != nullptr, lane, grp, sub, lt, lp);
+                                               PASS == PASS_COUNT && stats != nullptr, lane, grp, sub, lt, lp);
             // donate the older half of the stack when other warps are waiting
             if (top >= 2 && (steps & 3) == 0) {
                 unsigned long long h = 0, tl = 0;
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kThreads)
                 }
             }
         }
-        if (stats && lane == 0)
+        if (PASS == PASS_COUNT && stats && lane == 0)
             flush_stats(stats, wk, root == 0);
         if (lane == 0) {
             if (wk.overflow)
