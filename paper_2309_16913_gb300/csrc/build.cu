@@ -400,6 +400,20 @@ int bits_for(uint64_t v)  // bits needed to hold values 0..v
     return b;
 }
 
+// Allocates the leaf record (TreeDev::leaf_part) and fills it from the leaf
+// level's metadata, on stream s.
+rtree_status leaf_part_into(const int4 *leaf_meta, int64_t P, int F, DevBuf<int64_t> &part, cudaStream_t s)
+{
+    RT_TRY(part.alloc(3, "leaf record"));
+    RT_CUDA(cudaMemsetAsync(part.p, 0xff, sizeof(int64_t), s));
+    RT_CUDA(cudaMemsetAsync(part.p + 1, 0, 2 * sizeof(int64_t), s));
+    KernelTimer kt_("leaf_part", s);
+    k_leaf_part<<<blocks_for(P), kThreads, 0, s>>>(leaf_meta, P, F,
+                                                   reinterpret_cast<unsigned long long *>(part.p));
+    RT_LAUNCH();
+    return RTREE_OK;
+}
+
 }  // namespace
 
 rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int F, int layout,
@@ -585,6 +599,7 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     DevBuf<int4> meta(s);
     DevBuf<float4> nbox(s);
     DevBuf<int32_t> ids_out(s);
+    DevBuf<int64_t> part(s);  // the leaf record (TreeDev::leaf_part)
     RT_TRY(mbr.alloc((size_t)nodes * F * 4, "node entries"));
     RT_TRY(meta.alloc(nodes, "node metadata"));
     RT_TRY(nbox.alloc(nodes, "node boxes"));
@@ -632,6 +647,9 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
                 k_ranges_up<<<blocks_for(P), kThreads, 0, s>>>(meta.p, t->level_base[e], P);
             RT_LAUNCH();
         }
+        // the leaf record is filled before the root box is posted: the post's
+        // event is what calls on other streams wait for
+        RT_TRY(leaf_part_into(meta.p + t->level_base[H - 1], t->level_nodes[H - 1], F, part, s));
         // the root box goes to a mailbox of the tree, read when first asked
         // for (tree_root_box): the call does not wait for the packing
         Mailbox *mb = new Mailbox();
@@ -659,8 +677,9 @@ rtree_status build_tree(const float4 *rects, const int32_t *ids, int64_t n, int 
     t->meta = meta.release();
     t->nbox = nbox.release();
     t->ids = ids_out.release();
+    t->leaf_part = part.release();
     t->bytes = (int64_t)nodes * F * 16 + nodes * 32 + n * 4;
-    return compute_leaf_part(t, s);
+    return RTREE_OK;
 }
 
 rtree_status compute_leaf_part(rtree *t, cudaStream_t s)
@@ -668,16 +687,8 @@ rtree_status compute_leaf_part(rtree *t, cudaStream_t s)
     if (t->levels == 0)
         return RTREE_OK;
     DevBuf<int64_t> part(s);
-    RT_TRY(part.alloc(3, "leaf record"));
-    RT_CUDA(cudaMemsetAsync(part.p, 0xff, sizeof(int64_t), s));
-    RT_CUDA(cudaMemsetAsync(part.p + 1, 0, 2 * sizeof(int64_t), s));
-    const int64_t P = t->level_nodes[t->levels - 1];
-    {
-        KernelTimer kt_("leaf_part", s);
-        k_leaf_part<<<blocks_for(P), kThreads, 0, s>>>(t->meta + t->level_base[t->levels - 1], P, t->fanout,
-                                                       reinterpret_cast<unsigned long long *>(part.p));
-        RT_LAUNCH();
-    }
+    RT_TRY(leaf_part_into(t->meta + t->level_base[t->levels - 1], t->level_nodes[t->levels - 1], t->fanout,
+                          part, s));
     t->leaf_part = part.release();
     return RTREE_OK;
 }

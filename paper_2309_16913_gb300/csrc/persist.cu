@@ -420,7 +420,11 @@ rtree_status load_payload(FILE *f, const Header &h, rtree *t, cudaStream_t s)
     t->meta = meta.release();
     t->nbox = nbox.release();
     t->ids = ids.release();
-    return compute_leaf_part(t, s);
+    // the load returns with its work finished (calls on any stream may use
+    // the tree at once): wait for the leaf record too
+    RT_TRY(compute_leaf_part(t, s));
+    RT_CUDA(cudaStreamSynchronize(s));
+    return RTREE_OK;
 }
 
 }  // namespace
